@@ -1,0 +1,127 @@
+/*
+ * es.h -- C ABI of the GB300 locally relaxed entropy-stable RK step.
+ *
+ * Method: Ranocha, Dalcin & Parsani, "Fully-discrete explicit locally
+ * entropy-stable schemes for the compressible Euler and Navier--Stokes
+ * equations" (2020).  The library advances u' = f(u) (Eq. (ode)) where f is
+ * the SBP-SAT semidiscretisation of Eq. (compressible_ns_diss) on a periodic
+ * Cartesian mesh of LGL hexahedra, with an explicit Runge--Kutta method
+ * (Eq. (RK-step)) and the local relaxation of Eq. (relaxation-local-gamma)
+ * with gamma = min_kappa gamma_kappa (Theorem 2.3).
+ *
+ * Conventions (every entry point):
+ *  - Return 0 (ES_OK) or a negative ES_ERR_* code.  Argument errors are
+ *    detected on the host before anything is launched.
+ *  - Device pointers are CUDA device memory of the current device; they are
+ *    owned by the caller and never freed by the library.  The context owns its
+ *    workspace and frees it in es_destroy.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream).  Errors found on the device (non-physical state,
+ *    no relaxation root) are sticky bits read by es_status.
+ *  - State layout ("SoA"): double q[5][K][Np], variable v = rho, rho u1,
+ *    rho u2, rho u3, rho E; element e = ex + nx (ey + ny ez); node
+ *    n = i + (p+1) (j + (p+1) k) with (i, j, k) the LGL indices along
+ *    (x1, x2, x3).  K = nx ny nz, Np = (p+1)^3.
+ *  - Not thread-safe per context: one host thread drives a context at a time.
+ */
+#ifndef ES_H
+#define ES_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ES_OK 0
+#define ES_ERR_INVALID (-1)     /* bad argument or unsupported configuration */
+#define ES_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define ES_ERR_NONPHYSICAL (-3) /* rho <= 0 or p <= 0 met at some node */
+#define ES_ERR_NO_ROOT (-4)     /* an element had r'(0) >= 0: no positive gamma_kappa */
+#define ES_ERR_NOMEM (-6)       /* device or host allocation failed */
+
+#define ES_RK_BS3 0 /* Bogacki--Shampine 3(2), b = (2/9, 1/3, 4/9, 0) */
+#define ES_RK_RK4 1 /* classical RK(4,4) */
+
+#define ES_FP64 0  /* every operation in FP64 */
+#define ES_MIXED 1 /* FP32 fluxes/SATs/viscous terms; FP64 state, entropy sums, gamma solve */
+
+#define ES_RELAX_NONE 0  /* baseline RK, gamma = 1 */
+#define ES_RELAX_LOCAL 1 /* gamma = min_kappa gamma_kappa (Theorem 2.3) */
+
+typedef struct es_ctx es_ctx;
+
+typedef struct {
+  int p;                /* LGL degree, 2..5 */
+  int nx, ny, nz;       /* elements per direction, each >= 1 */
+  double lo[3], hi[3];  /* periodic box */
+  double gamma_gas;     /* ratio of specific heats, > 1 */
+  double mu;            /* dynamic viscosity; 0 = Euler (no viscous terms) */
+  double Pr;            /* Prandtl number (mu > 0) */
+  double R;             /* gas constant, p = rho R T */
+  int interface_diss;   /* 0: entropy-conservative SAT^I; 1: + Rusanov diss^I */
+  int relax;            /* ES_RELAX_* */
+  int rk;               /* ES_RK_* */
+  int precision;        /* ES_FP64 or ES_MIXED */
+  double delta_floor;   /* elements whose RMS relative change over the step is
+                           <= delta_floor are unconstrained (gamma_kappa = +inf);
+                           <= 0 selects 1e-8 */
+} es_config;
+
+/* Mesh, LGL/SBP tables (Section 3.1: diagonal-norm SBP on LGL nodes) and
+ * device workspace for one configuration.  Allocates device memory on the
+ * current device.  On error *out is NULL. */
+int es_create(const es_config* cfg, es_ctx** out);
+
+/* Frees the workspace; NULL is a no-op. Synchronises the device. */
+void es_destroy(es_ctx* ctx);
+
+/* f(q) of Eq. (ode): dqdt[5][K][Np] = the right-hand side of
+ * Eq. (compressible_ns_diss) (volume flux differencing 2 D o F 1, SAT^I
+ * (+ diss^I), BR1 viscous terms and SAT^V when mu > 0).  If E_elem is not
+ * NULL, E_elem[K] = (eta_kappa' f)(q) = sum_n P_n w(q_n).dqdt_n
+ * (the integrand of Eq. (eta-est-1-RK)).  q and dqdt must not overlap. */
+int es_rhs(es_ctx* ctx, const double* q, double* dqdt, double* E_elem, void* stream);
+
+/* eta_elem[K] = eta_kappa(q) = 1^T P S_kappa (Section 3.2), S = -rho s/(gamma-1). */
+int es_entropy(es_ctx* ctx, const double* q, double* eta_elem, void* stream);
+
+/* One relaxation (last row of Eq. (relaxation-local-gamma), Theorem 2.3):
+ * for every element the root gamma_elem[e] > 0 of
+ *   eta_e(u_old + g (u_new - u_old)) - eta_e(u_old) - g d_eta[e] = 0,
+ * then *gamma = min_e gamma_elem[e] (1 if no element is constrained) and
+ * u_out = u_old + gamma (u_new - u_old).  All pointers are device memory;
+ * u_out may alias u_new but not u_old.  Unconstrained elements report +inf. */
+int es_relax_step(es_ctx* ctx, const double* u_old, const double* u_new, const double* d_eta,
+                  double* gamma_elem, double* gamma, double* u_out, void* stream);
+
+/* nsteps relaxed RK steps of size dt (Eq. (RK-step) + Eq. (eta-est-1-RK) +
+ * Eq. (relaxation-local-gamma)), in place on q (device).  *t (device scalar)
+ * advances by gamma dt per step (Eq. (t-n-gamma)).  gamma_hist[nsteps]
+ * (device) receives each step's gamma if not NULL; gamma_elem[K] (device)
+ * receives the last step's gamma_kappa if not NULL. */
+int es_advance(es_ctx* ctx, double* q, int nsteps, double dt, double* t, double* gamma_hist,
+               double* gamma_elem, void* stream);
+
+/* es_advance on HOST buffers: copies q_host (5 K Np doubles) and *t_host to
+ * the context's device buffers, advances, and copies q, t and gamma_hist
+ * (nsteps doubles, may be NULL) back; returns after the stream completes.
+ * Pinned host memory makes the copies asynchronous DMA. */
+int es_advance_host(es_ctx* ctx, double* q_host, int nsteps, double dt, double* t_host,
+                    double* gamma_hist_host, void* stream);
+
+/* Node coordinates xyz[3][K][Np] (host memory), in the state layout. */
+int es_node_coords(const es_ctx* ctx, double* xyz_host);
+
+/* Synchronises `stream`, returns the first sticky device error
+ * (ES_ERR_NONPHYSICAL, ES_ERR_NO_ROOT) or ES_ERR_CUDA, and clears the bits. */
+int es_status(es_ctx* ctx, void* stream);
+
+/* Number of kernel launches the context has enqueued since es_create. */
+long long es_launch_count(const es_ctx* ctx);
+
+/* Static message for an ES_* code. */
+const char* es_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ES_H */

@@ -1,1 +1,9 @@
-"""GB300-native locally relaxed entropy-stable RK step (placeholder, filled below)."""
+"""GB300-native locally relaxed entropy-stable RK step (Ranocha, Dalcin & Parsani 2020).
+
+The compute path is the CUDA library ``libes.so`` (C ABI in ``include/es.h``);
+``_binding`` marshals torch tensors / numpy arrays to it, ``solver`` is a small
+convenience layer, ``inputs`` builds the synthetic initial states.
+"""
+from . import _binding  # noqa: F401
+from ._binding import (ES_FP64, ES_MIXED, ES_RELAX_LOCAL, ES_RELAX_NONE, ES_RK_BS3, ES_RK_RK4,  # noqa: F401
+                       ESError, make_config)

@@ -1,0 +1,178 @@
+"""ctypes binding of libes.so (include/es.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch tensors
+(device memory, streams) and numpy arrays (host buffers) to the plain pointers
+and sizes of the C ABI and raises on non-zero return codes.  If libes.so is
+missing or fails to load, every call raises: there is no fallback path.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libes.so")
+
+ES_OK = 0
+ES_ERR_INVALID = -1
+ES_ERR_CUDA = -2
+ES_ERR_NONPHYSICAL = -3
+ES_ERR_NO_ROOT = -4
+ES_ERR_NOMEM = -6
+ES_RK_BS3, ES_RK_RK4 = 0, 1
+ES_FP64, ES_MIXED = 0, 1
+ES_RELAX_NONE, ES_RELAX_LOCAL = 0, 1
+
+EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "es_advance",
+           "es_advance_host", "es_node_coords", "es_status", "es_launch_count", "es_strerror"]
+
+
+class es_config(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("gamma_gas", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("R", ctypes.c_double), ("interface_diss", ctypes.c_int), ("relax", ctypes.c_int),
+                ("rk", ctypes.c_int), ("precision", ctypes.c_int), ("delta_floor", ctypes.c_double)]
+
+
+class ESError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__("%s failed: %s (%d)" % (where, strerror(code), code))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load libes.so once; raise if it is absent (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libes.so not found at %s: build it with paper_2003_08831_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
+    lib.es_create.argtypes = [ctypes.POINTER(es_config), ctypes.POINTER(vp)]
+    lib.es_create.restype = i
+    lib.es_destroy.argtypes = [vp]
+    lib.es_destroy.restype = None
+    lib.es_rhs.argtypes = [vp, vp, vp, vp, vp]
+    lib.es_rhs.restype = i
+    lib.es_entropy.argtypes = [vp, vp, vp, vp]
+    lib.es_entropy.restype = i
+    lib.es_relax_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.es_relax_step.restype = i
+    lib.es_advance.argtypes = [vp, vp, i, d, vp, vp, vp, vp]
+    lib.es_advance.restype = i
+    lib.es_advance_host.argtypes = [vp, vp, i, d, vp, vp, vp]
+    lib.es_advance_host.restype = i
+    lib.es_node_coords.argtypes = [vp, vp]
+    lib.es_node_coords.restype = i
+    lib.es_status.argtypes = [vp, vp]
+    lib.es_status.restype = i
+    lib.es_launch_count.argtypes = [vp]
+    lib.es_launch_count.restype = ctypes.c_longlong
+    lib.es_strerror.argtypes = [i]
+    lib.es_strerror.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def strerror(code):
+    try:
+        return load().es_strerror(int(code)).decode()
+    except Exception:
+        return "error %d" % code
+
+
+def _check(rc, where):
+    if rc != ES_OK:
+        raise ESError(rc, where)
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor, host pointer of a numpy array, or None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    if hasattr(t, "ctypes"):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(t.ctypes.data)
+    raise TypeError("expected a torch tensor or numpy array")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def make_config(p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0,
+                interface_diss=1, relax=ES_RELAX_LOCAL, rk=ES_RK_BS3, precision=ES_FP64, delta_floor=1e-8):
+    c = es_config()
+    c.p = p
+    c.nx, c.ny, c.nz = n
+    c.lo = (ctypes.c_double * 3)(*lo)
+    c.hi = (ctypes.c_double * 3)(*hi)
+    c.gamma_gas, c.mu, c.Pr, c.R = gamma_gas, mu, Pr, R
+    c.interface_diss, c.relax, c.rk, c.precision = interface_diss, relax, rk, precision
+    c.delta_floor = delta_floor
+    return c
+
+
+# ---- the C ABI under the same names -------------------------------------------------------
+
+def es_create(cfg):
+    ctx = ctypes.c_void_p()
+    _check(load().es_create(ctypes.byref(cfg), ctypes.byref(ctx)), "es_create")
+    return ctx
+
+
+def es_destroy(ctx):
+    load().es_destroy(ctx)
+
+
+def es_rhs(ctx, q, dqdt, E_elem=None, stream=None):
+    _check(load().es_rhs(ctx, _ptr(q), _ptr(dqdt), _ptr(E_elem), _stream(stream)), "es_rhs")
+
+
+def es_entropy(ctx, q, eta_elem, stream=None):
+    _check(load().es_entropy(ctx, _ptr(q), _ptr(eta_elem), _stream(stream)), "es_entropy")
+
+
+def es_relax_step(ctx, u_old, u_new, d_eta, gamma_elem, gamma, u_out, stream=None):
+    _check(load().es_relax_step(ctx, _ptr(u_old), _ptr(u_new), _ptr(d_eta), _ptr(gamma_elem), _ptr(gamma),
+                                _ptr(u_out), _stream(stream)), "es_relax_step")
+
+
+def es_advance(ctx, q, nsteps, dt, t, gamma_hist=None, gamma_elem=None, stream=None):
+    _check(load().es_advance(ctx, _ptr(q), int(nsteps), float(dt), _ptr(t), _ptr(gamma_hist), _ptr(gamma_elem),
+                             _stream(stream)), "es_advance")
+
+
+def es_advance_host(ctx, q_host, nsteps, dt, t_host, gamma_hist_host=None, stream=None):
+    _check(load().es_advance_host(ctx, _ptr(q_host), int(nsteps), float(dt), _ptr(t_host), _ptr(gamma_hist_host),
+                                  _stream(stream)), "es_advance_host")
+
+
+def es_node_coords(ctx, xyz_host):
+    _check(load().es_node_coords(ctx, _ptr(xyz_host)), "es_node_coords")
+
+
+def es_status(ctx, stream=None):
+    return load().es_status(ctx, _stream(stream))
+
+
+def es_launch_count(ctx):
+    return int(load().es_launch_count(ctx))
+
+
+def es_strerror(code):
+    return strerror(code)

@@ -1,0 +1,235 @@
+// Device-side building blocks of the locally relaxed entropy-stable RK step.
+//
+// Pointwise thermodynamics of Section 3.1 (conserved q = (rho, rho U, rho E),
+// P = rho R T, entropy S = -rho s with s = ln p - gamma ln rho, scaled by
+// 1/(gamma - 1)), the Ismail--Roe entropy-conservative two-point flux with the
+// series logarithmic mean, Rusanov interface dissipation, and the
+// cancellation-free pieces of the relaxation function of
+// Eq. (relaxation-local-gamma).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace es {
+
+constexpr int kMaxP1 = 6;
+constexpr int kStatusNonphysical = 1;
+constexpr int kStatusNoRoot = 2;
+
+// Operator tables and physics constants, passed by value to every kernel.
+struct Params {
+  double D[kMaxP1 * kMaxP1];   // SBP derivative on [-1, 1], row-major
+  double D2[kMaxP1 * kMaxP1];  // 2 D_ij (i != j), 0 on the diagonal
+  double omega[kMaxP1];        // LGL weights
+  double inv_omega_end;        // 1/omega_0 = 1/omega_p
+  double metric[3];            // 2/h_m
+  double J;                    // h1 h2 h3 / 8
+  double gam;                  // ratio of specific heats
+  double mu, kappa_heat, R;    // viscosity, heat conductivity mu c_p / Pr, gas constant
+  int nx, ny, nz, K;
+  int diss;                    // Rusanov interface dissipation on/off
+  int p1;                      // p + 1
+};
+
+// ---------------------------------------------------------------------------
+// element / node index helpers
+__device__ __forceinline__ int neighbour(const Params& P, int e, int m, int dir) {
+  int ex = e % P.nx;
+  int ey = (e / P.nx) % P.ny;
+  int ez = e / (P.nx * P.ny);
+  if (m == 0) ex = (ex + dir + P.nx) % P.nx;
+  else if (m == 1) ey = (ey + dir + P.ny) % P.ny;
+  else ez = (ez + dir + P.nz) % P.nz;
+  return ex + P.nx * (ey + P.ny * ez);
+}
+
+// node index of position i on the line (a, b) in direction m
+template <int P1>
+__device__ __forceinline__ int line_node(int m, int a, int b, int i) {
+  return m == 0 ? i + P1 * (a + P1 * b) : (m == 1 ? a + P1 * (i + P1 * b) : a + P1 * (b + P1 * i));
+}
+
+// mass weight P_n = J omega_i omega_j omega_k
+template <int P1>
+__device__ __forceinline__ double mass_weight(const Params& P, int n) {
+  int i = n % P1, j = (n / P1) % P1, k = n / (P1 * P1);
+  return P.J * P.omega[i] * P.omega[j] * P.omega[k];
+}
+
+// ---------------------------------------------------------------------------
+// Parameter-vector state used by the two-point flux: z = sqrt(rho/p) (1, v, p)
+// plus ln z1 and ln z5.  Layout of the 7 values: z1, z2, z3, z4, z5, lz1, lz5.
+template <typename T>
+struct Zstate {
+  T z[5];
+  T lz1, lz5;
+};
+
+// Series logarithmic-mean pieces.  For aL, aR > 0 with s = aL + aR,
+// d = aL - aR and u = (d/s)^2:  ln-mean = (s/2) / F(u) with
+// F(u) = atanh(sqrt u)/sqrt u = 1 + u/3 + u^2/5 + u^3/7 + ...  Below the
+// threshold both F and 1/F are taken from their Taylor series (truncation
+// below the type's rounding); above it the mean is d / (ln aL - ln aR).
+template <typename T> struct LogMeanConst;
+template <> struct LogMeanConst<double> { static constexpr double eps = 1.0e-4; };
+template <> struct LogMeanConst<float> { static constexpr float eps = 1.0e-2f; };
+
+template <typename T>
+__device__ __forceinline__ T series_F(T u) {  // 1 + u/3 + u^2/5 + u^3/7
+  return T(1) + u * (T(1.0 / 3.0) + u * (T(1.0 / 5.0) + u * T(1.0 / 7.0)));
+}
+template <typename T>
+__device__ __forceinline__ T series_invF(T u) {  // 1/F = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
+  return T(1) - u * (T(1.0 / 3.0) + u * (T(4.0 / 45.0) + u * T(44.0 / 945.0)));
+}
+
+// Constants of the gas law used by the flux, in the flux's precision.
+template <typename T>
+struct FluxConst {
+  T gam, c1, c2, g_gm1, inv_gm1, sqrt_gam;
+  __host__ __device__ static FluxConst make(double g) {
+    FluxConst c;
+    c.gam = T(g);
+    c.c1 = T((g + 1.0) / (2.0 * g));
+    c.c2 = T((g - 1.0) / (2.0 * g));
+    c.g_gm1 = T(g / (g - 1.0));
+    c.inv_gm1 = T(1.0 / (g - 1.0));
+    c.sqrt_gam = T(sqrt(g));
+    return c;
+  }
+};
+
+// Ismail--Roe two-point flux in direction m between states a and b.
+template <typename T>
+__device__ __forceinline__ void ec_flux(const Zstate<T>& a, const Zstate<T>& b, int m, const FluxConst<T>& C,
+                                        T f[5]) {
+  const T S1 = a.z[0] + b.z[0], D1 = a.z[0] - b.z[0];
+  const T S5 = a.z[4] + b.z[4], D5 = a.z[4] - b.z[4];
+  const T inv = T(1) / (S1 * S5);
+  const T inv1 = S5 * inv;          // 1/S1
+  const T r1 = D1 * inv1;
+  const T r5 = D5 * (S1 * inv);     // D5/S5
+  const T u1 = r1 * r1, u5 = r5 * r5;
+  const T eps = LogMeanConst<T>::eps;
+  // 1 / ln-mean(z1) and ln-mean(z5)
+  T inv_lm1, lm5;
+  if (u1 < eps) inv_lm1 = T(2) * series_F(u1) * inv1;
+  else inv_lm1 = (a.lz1 - b.lz1) / D1;
+  if (u5 < eps) lm5 = T(0.5) * S5 * series_invF(u5);
+  else lm5 = D5 / (a.lz5 - b.lz5);
+  const T zb1 = T(0.5) * S1;
+  const T rho_hat = zb1 * lm5;
+  const T u0 = (a.z[1] + b.z[1]) * inv1;
+  const T uy = (a.z[2] + b.z[2]) * inv1;
+  const T uz = (a.z[3] + b.z[3]) * inv1;
+  const T p1 = S5 * inv1;
+  const T p2 = C.c1 * lm5 * inv_lm1 + C.c2 * p1;
+  const T um = m == 0 ? u0 : (m == 1 ? uy : uz);
+  const T mass = rho_hat * um;
+  const T q2 = u0 * u0 + uy * uy + uz * uz;
+  f[0] = mass;
+  f[1] = mass * u0;
+  f[2] = mass * uy;
+  f[3] = mass * uz;
+  f[1 + m] += p1;
+  // rho_hat u_m h_hat with h_hat = gam p2/((gam-1) rho_hat) + |u|^2/2
+  f[4] = um * C.g_gm1 * p2 + T(0.5) * mass * q2;
+}
+
+// Conserved state from the parameter vector: rho = z1 z5, v = z_{2..4}/z1,
+// p = z5/z1, c = sqrt(gam)/z1.
+template <typename T>
+__device__ __forceinline__ void z_to_q(const Zstate<T>& s, const FluxConst<T>& C, T q[5], T& vn_abs_plus_c, int m) {
+  const T iz1 = T(1) / s.z[0];
+  const T rho = s.z[0] * s.z[4];
+  const T v0 = s.z[1] * iz1, v1 = s.z[2] * iz1, v2 = s.z[3] * iz1;
+  const T p = s.z[4] * iz1;
+  q[0] = rho;
+  q[1] = rho * v0;
+  q[2] = rho * v1;
+  q[3] = rho * v2;
+  q[4] = p * C.inv_gm1 + T(0.5) * rho * (v0 * v0 + v1 * v1 + v2 * v2);
+  const T vm = m == 0 ? v0 : (m == 1 ? v1 : v2);
+  vn_abs_plus_c = fabs(vm) + C.sqrt_gam * iz1;
+}
+
+// Entropy variables from the parameter vector:
+// w = ((gam - s)/(gam-1) - |zv|^2/2, z1 zv, -z1^2), s = -(gam+1) ln z1 - (gam-1) ln z5.
+template <typename T>
+__device__ __forceinline__ void z_to_w(const Zstate<T>& s, const FluxConst<T>& C, T w[5]) {
+  const T sp = -(C.gam + T(1)) * s.lz1 - (C.gam - T(1)) * s.lz5;
+  w[0] = (C.gam - sp) * C.inv_gm1 - T(0.5) * (s.z[1] * s.z[1] + s.z[2] * s.z[2] + s.z[3] * s.z[3]);
+  w[1] = s.z[0] * s.z[1];
+  w[2] = s.z[0] * s.z[2];
+  w[3] = s.z[0] * s.z[3];
+  w[4] = -s.z[0] * s.z[0];
+}
+
+// ---------------------------------------------------------------------------
+// log(1 + z) - z without cancellation.  For |z| <= 0.1: with t = z/(2+z),
+// log1p(z) = 2 atanh(t) = 2 (t + t^3/3 + t^5/5 + ...) and z = 2t/(1-t), so
+// log1p(z) - z = -t z + 2 t^3 (1/3 + t^2/5 + t^4/7 + ...); |t| < 0.053 and
+// seven terms of the even series reach 1e-17 relative.  Otherwise the direct
+// difference, whose cancellation costs at most a factor 20 in relative error.
+__device__ __forceinline__ double log1pmx(double z) {
+  if (fabs(z) <= 0.1) {
+    const double t = z / (2.0 + z);
+    const double t2 = t * t;
+    double s = 1.0 / 17.0;
+    s = s * t2 + 1.0 / 15.0;
+    s = s * t2 + 1.0 / 13.0;
+    s = s * t2 + 1.0 / 11.0;
+    s = s * t2 + 1.0 / 9.0;
+    s = s * t2 + 1.0 / 7.0;
+    s = s * t2 + 1.0 / 5.0;
+    s = s * t2 + 1.0 / 3.0;
+    return -t * z + 2.0 * t * t2 * s;
+  }
+  return log1p(z) - z;
+}
+
+// Per-node inputs of the relaxation function (see the relaxation kernel):
+// X0 = d_rho/rho, Y0 = linearised d_p/p, V2 = rho |d_v|^2/p, c = P_n rho.
+struct RelaxNode {
+  double X0, Y0, V2, c;
+};
+
+// D_breg/rho at gamma and its gamma-derivative for one node:
+//   x = g X0, K = g^2 V2/(2(1+x)), y = g Y0 - (gam-1) K,
+//   D/rho = [gam phi(x) + psi(y) - x log1p(y)]/(gam-1) + K,
+//   phi(x) = (1+x) log1p(x) - x, psi(y) = y - log1p(y);
+//   d/dg (D/rho) = [X0 (gam log1p(x) - log1p(y)) + y' (y - x)/(1+y)]/(gam-1) + K',
+//   K' = g V2/(1+x) (1 - x/(2(1+x))), y' = Y0 - (gam-1) K'.
+// Returns false if the state at gamma is not physical (1+x <= 0 or 1+y <= 0).
+__device__ __forceinline__ bool relax_node_eval(const RelaxNode& nd, double g, double gam, double& D,
+                                                double& dD) {
+  const double x = g * nd.X0;
+  if (!(x > -1.0)) return false;
+  const double q = 1.0 / (1.0 + x);
+  const double K = 0.5 * g * g * nd.V2 * q;
+  const double y = g * nd.Y0 - (gam - 1.0) * K;
+  if (!(y > -1.0)) return false;
+  const double Lx = log1pmx(x), Ly = log1pmx(y);
+  const double l1px = x + Lx, l1py = y + Ly;
+  const double phi = (1.0 + x) * Lx + x * x;
+  D = (gam * phi - Ly - x * l1py) / (gam - 1.0) + K;
+  const double dK = g * nd.V2 * q * (1.0 - 0.5 * x * q);
+  const double dy = nd.Y0 - (gam - 1.0) * dK;
+  dD = (nd.X0 * (gam * l1px - l1py) + dy * (y - x) / (1.0 + y)) / (gam - 1.0) + dK;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// warp reductions (butterfly: every lane ends with the same sum/min)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// positive doubles (and +inf) order like their bit patterns as unsigned integers
+__device__ __forceinline__ void atomic_min_positive(unsigned long long* addr, double v) {
+  atomicMin(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace es

@@ -1,0 +1,615 @@
+// Kernels of one relaxed RK step (templated on the LGL point count P1 = p+1
+// and on the flux precision TF).  Each per-P1 translation unit instantiates
+// them through the launchers at the bottom.
+//
+// Stage pipeline (Eq. (RK-step), Eq. (compressible_ns_diss)):
+//   k_prep    y^i = u + dt sum_j a_ij k_j (fused relaxed update of the previous
+//             step), parameter-vector state z, ln z1, ln z5 per node; for i > 1
+//             the increment w(y^i) - w(u) of the entropy variables.
+//   k_face    interface flux f*(q-, q+) - diss lambda/2 (q+ - q-) per face node.
+//   k_grad    (Navier--Stokes) BR1 entropy-variable gradients and the viscous
+//             flux F^V_m = C_mj theta_j per node.
+//   k_volume  per element: flux-differencing sums along every LGL line,
+//             interface terms, viscous divergence; k_i, and the element sums
+//             (eta' f)(y^i) (Eq. (eta-est-1-RK)) and the relaxation term A.
+//   k_relax   per element (one warp): gamma_kappa of
+//             Eq. (relaxation-local-gamma); atomic min into gamma.
+//   k_scalar  gamma = min gamma_kappa, t += gamma dt (Eq. (t-n-gamma)).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "es_device.cuh"
+#include "es_launch.h"
+
+namespace es {
+
+// elements per CTA of the volume kernel and its thread count
+template <int P1> struct VolCfg;
+template <> struct VolCfg<3> { static constexpr int EPB = 32, THREADS = 288; };
+template <> struct VolCfg<4> { static constexpr int EPB = 8, THREADS = 128; };
+template <> struct VolCfg<5> { static constexpr int EPB = 5, THREADS = 128; };
+template <> struct VolCfg<6> { static constexpr int EPB = 4, THREADS = 160; };
+
+// ---------------------------------------------------------------------------
+// accurate w(u + e) - w(u) from the increment e (no cancellation):
+// x = e_rho/rho, dv = (e_m - v e_rho)/(rho + e_rho),
+// y = (p' - p)/p = (gam-1)[e_E - v.e_m + |v|^2 e_rho/2 - (rho + e_rho)|dv|^2/2]/p,
+// beta = rho/p, ds = log1p(y) - gam log1p(x),
+// dw1 = -ds/(gam-1) - beta[(x-y)|v|^2 + (1+x)(2 v.dv + |dv|^2)]/(2(1+y)),
+// dw_v = beta[(x-y) v + (1+x) dv]/(1+y), dw5 = -beta (x-y)/(1+y).
+__device__ __forceinline__ void entropy_var_increment(const double u[5], const double e[5], double gam,
+                                                      double dw[5]) {
+  const double rho = u[0];
+  const double ir = 1.0 / rho;
+  const double v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
+  const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
+  const double p = (gam - 1.0) * (u[4] - 0.5 * rho * v2s);
+  const double x = e[0] * ir;
+  const double rho1 = rho + e[0];
+  const double ir1 = 1.0 / rho1;
+  const double d0 = (e[1] - v0 * e[0]) * ir1, d1 = (e[2] - v1 * e[0]) * ir1, d2 = (e[3] - v2 * e[0]) * ir1;
+  const double dv2 = d0 * d0 + d1 * d1 + d2 * d2;
+  const double ip = 1.0 / p;
+  const double y =
+      (gam - 1.0) * (e[4] - (v0 * e[1] + v1 * e[2] + v2 * e[3]) + 0.5 * v2s * e[0] - 0.5 * rho1 * dv2) * ip;
+  const double beta = rho * ip;
+  const double iy = 1.0 / (1.0 + y);
+  const double ds = log1p(y) - gam * log1p(x);
+  const double xy = x - y;
+  const double dkin = 0.5 * beta * (xy * v2s + (1.0 + x) * (2.0 * (v0 * d0 + v1 * d1 + v2 * d2) + dv2)) * iy;
+  dw[0] = -ds / (gam - 1.0) - dkin;
+  dw[1] = beta * (xy * v0 + (1.0 + x) * d0) * iy;
+  dw[2] = beta * (xy * v1 + (1.0 + x) * d1) * iy;
+  dw[3] = beta * (xy * v2 + (1.0 + x) * d2) * iy;
+  dw[4] = -beta * xy * iy;
+}
+
+// ---------------------------------------------------------------------------
+template <typename TF>
+__global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __restrict__ status) {
+  const long long N = (long long)P.K * sp.Np;
+  const double gam = P.gam;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    double u[5], y[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = sp.q[v * N + g];
+    if (sp.apply_update) {
+      const double gmm = *sp.gamma_cur;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        u[v] = u[v] + gmm * sp.d[v * N + g];
+        sp.q[v * N + g] = u[v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) y[v] = u[v];
+    for (int j = 0; j < sp.nprev; ++j) {
+      const double c = sp.coef[j];
+      const double* kj = sp.k[j];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) y[v] = fma(c, kj[v * N + g], y[v]);
+    }
+    const double rho = y[0];
+    const double ir = 1.0 / rho;
+    const double v0 = y[1] * ir, v1 = y[2] * ir, v2 = y[3] * ir;
+    const double p = (gam - 1.0) * (y[4] - 0.5 * rho * (v0 * v0 + v1 * v1 + v2 * v2));
+    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(status, kStatusNonphysical);
+    if constexpr (sizeof(TF) == 8) {
+      const double z1 = sqrt(rho / p);
+      const double lr = log(rho), lp = log(p);
+      aux[0 * N + g] = z1;
+      aux[1 * N + g] = z1 * v0;
+      aux[2 * N + g] = z1 * v1;
+      aux[3 * N + g] = z1 * v2;
+      aux[4 * N + g] = rho / z1;       // sqrt(rho p)
+      aux[5 * N + g] = 0.5 * (lr - lp);
+      aux[6 * N + g] = 0.5 * (lr + lp);
+    } else {
+      const float rf = float(rho), pf = float(p);
+      const float z1 = sqrtf(rf / pf);
+      const float lr = logf(rf), lp = logf(pf);
+      aux[0 * N + g] = z1;
+      aux[1 * N + g] = z1 * float(v0);
+      aux[2 * N + g] = z1 * float(v1);
+      aux[3 * N + g] = z1 * float(v2);
+      aux[4 * N + g] = rf / z1;
+      aux[5 * N + g] = 0.5f * (lr - lp);
+      aux[6 * N + g] = 0.5f * (lr + lp);
+    }
+    if (sp.dw) {
+      double e[5], dw[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) e[v] = y[v] - u[v];
+      entropy_var_increment(u, e, gam, dw);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sp.dw[v * N + g] = dw[v];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int P1, typename TF>
+__device__ __forceinline__ Zstate<TF> load_z(const TF* __restrict__ aux, long long N, long long g) {
+  Zstate<TF> s;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) s.z[c] = aux[c * N + g];
+  s.lz1 = aux[5 * N + g];
+  s.lz5 = aux[6 * N + g];
+  return s;
+}
+
+template <int P1, typename TF>
+__global__ void k_face(Params P, const TF* __restrict__ aux, TF* __restrict__ F) {
+  constexpr int P2 = P1 * P1, Np = P1 * P2;
+  const long long N = (long long)P.K * Np;
+  const long long total = 3LL * P.K * P2;
+  const FluxConst<TF> C = FluxConst<TF>::make(P.gam);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m = int(idx / ((long long)P.K * P2));
+    const long long rem = idx - (long long)m * P.K * P2;
+    const int e = int(rem / P2), ab = int(rem % P2);
+    const int a = ab % P1, b = ab / P1;
+    const int en = neighbour(P, e, m, +1);
+    const Zstate<TF> L = load_z<P1, TF>(aux, N, (long long)e * Np + line_node<P1>(m, a, b, P1 - 1));
+    const Zstate<TF> R = load_z<P1, TF>(aux, N, (long long)en * Np + line_node<P1>(m, a, b, 0));
+    TF f[5];
+    ec_flux(L, R, m, C, f);
+    if (P.diss) {
+      TF qL[5], qR[5], lL, lR;
+      z_to_q(L, C, qL, lL, m);
+      z_to_q(R, C, qR, lR, m);
+      const TF lam = TF(0.5) * fmax(lL, lR);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f[v] -= lam * (qR[v] - qL[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[((long long)(m * 5 + v) * P.K + e) * P2 + ab] = f[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// BR1 gradients and viscous flux per node.  fV[(m*4 + c) N + g], c = momentum
+// x, y, z, energy.  theta_m = (2/h_m) [D w + (1/omega) (w_face_avg - w) n_m].
+template <int P1, typename TF>
+__global__ void k_grad(Params P, const TF* __restrict__ aux, TF* __restrict__ fV) {
+  constexpr int P2 = P1 * P1, Np = P1 * P2;
+  const long long N = (long long)P.K * Np;
+  const FluxConst<TF> C = FluxConst<TF>::make(P.gam);
+  const TF mu = TF(P.mu), kap = TF(P.kappa_heat), Rg = TF(P.R);
+  const TF iw = TF(P.inv_omega_end);
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    const int e = int(g / Np), n = int(g % Np);
+    const int ii[3] = {n % P1, (n / P1) % P1, n / P2};
+    TF th[3][4];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const int im = ii[m];
+      const int a = m == 0 ? ii[1] : ii[0];
+      const int b = m == 2 ? ii[1] : ii[2];
+      TF acc[4] = {TF(0), TF(0), TF(0), TF(0)};
+#pragma unroll
+      for (int j = 0; j < P1; ++j) {
+        const Zstate<TF> s = load_z<P1, TF>(aux, N, (long long)e * Np + line_node<P1>(m, a, b, j));
+        TF w[5];
+        z_to_w(s, C, w);
+        const TF Dij = TF(P.D[im * P1 + j]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += Dij * w[1 + c];
+      }
+      if (im == P1 - 1 || im == 0) {
+        const bool right = (im == P1 - 1);
+        const int en = neighbour(P, e, m, right ? +1 : -1);
+        const Zstate<TF> sn = load_z<P1, TF>(aux, N, (long long)en * Np + line_node<P1>(m, a, b, right ? 0 : P1 - 1));
+        const Zstate<TF> ss = load_z<P1, TF>(aux, N, g);
+        TF wn[5], ws[5];
+        z_to_w(sn, C, wn);
+        z_to_w(ss, C, ws);
+        const TF sg = right ? TF(0.5) * iw : TF(-0.5) * iw;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += sg * (wn[1 + c] - ws[1 + c]);
+      }
+      const TF met = TF(P.metric[m]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) th[m][c] = met * acc[c];
+    }
+    // chain rule: v = -w_{2..4}/w_5, T = -1/(R w_5)
+    const Zstate<TF> s = load_z<P1, TF>(aux, N, g);
+    const TF z1 = s.z[0];
+    const TF iz1 = TF(1) / z1;
+    const TF v[3] = {s.z[1] * iz1, s.z[2] * iz1, s.z[3] * iz1};
+    const TF w5 = -z1 * z1;
+    const TF iw5 = TF(1) / w5;
+    TF gv[3][3], gT[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gv[m][k] = -(th[m][k] + v[k] * th[m][3]) * iw5;
+      gT[m] = th[m][3] * iw5 * iw5 / Rg;
+    }
+    const TF divv = gv[0][0] + gv[1][1] + gv[2][2];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      TF fe = kap * gT[m];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        TF tau = mu * (gv[m][k] + gv[k][m]);
+        if (k == m) tau -= mu * TF(2.0 / 3.0) * divv;
+        fV[(long long)(m * 4 + k) * N + g] = tau;
+        fe += tau * v[k];
+      }
+      fV[(long long)(m * 4 + 3) * N + g] = fe;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int P1, typename TF, bool NS>
+__global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageVol sv, const TF* __restrict__ aux,
+                                                             const TF* __restrict__ F, const TF* __restrict__ fV) {
+  constexpr int P2 = P1 * P1, Np = P1 * P2;
+  constexpr int EPB = VolCfg<P1>::EPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TF* za = reinterpret_cast<TF*>(smem_raw);            // [7][EPB*Np]
+  TF* acc = za + 7 * EPB * Np;                          // [5][EPB*Np]
+  double* red = reinterpret_cast<double*>(acc + 5 * EPB * Np);  // [2][EPB*Np]
+  const long long N = (long long)P.K * Np;
+  const int e0 = blockIdx.x * EPB;
+  const int nel = min(EPB, P.K - e0);
+  const int nn = nel * Np;
+  const FluxConst<TF> C = FluxConst<TF>::make(P.gam);
+  const TF iw = TF(P.inv_omega_end);
+
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 7; ++c) za[c * EPB * Np + t] = aux[c * N + (long long)e0 * Np + t];
+  }
+  __syncthreads();
+
+#pragma unroll 1
+  for (int m = 0; m < 3; ++m) {
+    const TF met = TF(P.metric[m]);
+    for (int l = threadIdx.x; l < nel * P2; l += blockDim.x) {
+      const int el = l / P2, ab = l % P2;
+      const int a = ab % P1, b = ab / P1;
+      const int e = e0 + el;
+      Zstate<TF> z[P1];
+#pragma unroll
+      for (int i = 0; i < P1; ++i) {
+        const int n = el * Np + line_node<P1>(m, a, b, i);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) z[i].z[c] = za[c * EPB * Np + n];
+        z[i].lz1 = za[5 * EPB * Np + n];
+        z[i].lz5 = za[6 * EPB * Np + n];
+      }
+      TF r[P1][5];
+#pragma unroll
+      for (int i = 0; i < P1; ++i)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) r[i][v] = TF(0);
+#pragma unroll
+      for (int i = 0; i < P1; ++i) {
+#pragma unroll
+        for (int j = i + 1; j < P1; ++j) {
+          TF f[5];
+          ec_flux(z[i], z[j], m, C, f);
+          const TF dij = TF(P.D2[i * P1 + j]), dji = TF(P.D2[j * P1 + i]);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            r[i][v] += dij * f[v];
+            r[j][v] += dji * f[v];
+          }
+        }
+      }
+      // interface terms: + (1/omega_p) f_num(+face) at i = p, - (1/omega_0) f_num(-face) at i = 0
+      const int em = neighbour(P, e, m, -1);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        r[P1 - 1][v] += iw * F[((long long)(m * 5 + v) * P.K + e) * P2 + ab];
+        r[0][v] -= iw * F[((long long)(m * 5 + v) * P.K + em) * P2 + ab];
+      }
+      if constexpr (NS) {
+        // viscous divergence (2/h_m)[D F^V_m + lifting]; enters with the opposite sign of r
+        const int ep = neighbour(P, e, m, +1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const TF* fc = fV + (long long)(m * 4 + c) * N;
+          TF fl[P1];
+#pragma unroll
+          for (int j = 0; j < P1; ++j) fl[j] = fc[(long long)e * Np + line_node<P1>(m, a, b, j)];
+          const TF f_next = fc[(long long)ep * Np + line_node<P1>(m, a, b, 0)];
+          const TF f_prev = fc[(long long)em * Np + line_node<P1>(m, a, b, P1 - 1)];
+#pragma unroll
+          for (int i = 0; i < P1; ++i) {
+            TF s = TF(0);
+#pragma unroll
+            for (int j = 0; j < P1; ++j) s += TF(P.D[i * P1 + j]) * fl[j];
+            if (i == P1 - 1) s += TF(0.5) * iw * (f_next - fl[P1 - 1]);
+            if (i == 0) s -= TF(0.5) * iw * (f_prev - fl[0]);
+            r[i][1 + c] -= s;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < P1; ++i) {
+        const int n = el * Np + line_node<P1>(m, a, b, i);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const TF val = -met * r[i][v];
+          acc[v * EPB * Np + n] = (m == 0) ? val : acc[v * EPB * Np + n] + val;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // node phase: write k_i, element sums
+  const bool wantE = sv.E != nullptr;
+  const bool wantA = sv.dw != nullptr;
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+    const long long g = (long long)e0 * Np + t;
+    const int n = t % Np;
+    double k[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      k[v] = double(acc[v * EPB * Np + t]);
+      sv.kout[v * N + g] = k[v];
+    }
+    const double Pn = mass_weight<P1>(P, n);
+    if (wantE) {
+      Zstate<TF> s;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) s.z[c] = za[c * EPB * Np + t];
+      s.lz1 = za[5 * EPB * Np + t];
+      s.lz5 = za[6 * EPB * Np + t];
+      TF w[5];
+      z_to_w(s, C, w);
+      double sum = 0.0;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sum += double(w[v]) * k[v];
+      red[t] = Pn * sum;
+    }
+    if (wantA) {
+      double sum = 0.0;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sum += sv.dw[v * N + g] * k[v];
+      red[EPB * Np + t] = Pn * sum;
+    }
+  }
+  const bool doA = sv.A != nullptr && (wantA || sv.A_init);
+  if (!wantE && !doA) return;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int el = warp; el < nel; el += blockDim.x >> 5) {
+    double sE = 0.0, sA = 0.0;
+    for (int n = lane; n < Np; n += 32) {
+      if (wantE) sE += red[el * Np + n];
+      if (wantA) sA += red[EPB * Np + el * Np + n];
+    }
+    sE = warp_sum(sE);
+    sA = warp_sum(sA);
+    if (lane == 0) {
+      const int e = e0 + el;
+      if (wantE) sv.E[e] = sE;
+      if (doA) sv.A[e] = (sv.A_init ? 0.0 : sv.A[e]) + (wantA ? sv.A_scale * sA : 0.0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Relaxation (one warp per element).  Per node: X0 = d_rho/rho,
+// dv = (d_m - v d_rho)/rho, Y0 = (gam-1)(d_E - v.d_m + |v|^2 d_rho/2)/p,
+// V2 = rho |dv|^2/p, c = P_n rho.  r(g) = sum_n c D_n(g)/rho_n + g A,
+// r'(g) = sum_n c dD_n/dg + A; a = r''(0)/2 = sum c (X0^2 + (X0-Y0)^2/(gam-1) + V2)/2.
+template <int P1>
+__global__ void k_relax(Params P, StageRelax sr) {
+  constexpr int Np = P1 * P1 * P1;
+  constexpr int R = (Np + 31) / 32;
+  const long long N = (long long)P.K * Np;
+  const double gam = P.gam;
+  const int lane = threadIdx.x & 31;
+  const int warps_per_block = blockDim.x >> 5;
+  for (int e = blockIdx.x * warps_per_block + (threadIdx.x >> 5); e < P.K; e += gridDim.x * warps_per_block) {
+    RelaxNode nd[R];
+    double a_part = 0.0, s_part = 0.0, A_part = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = lane + 32 * r;
+      nd[r].X0 = nd[r].Y0 = nd[r].V2 = nd[r].c = 0.0;
+      if (n < Np) {
+        const long long g = (long long)e * Np + n;
+        double u[5], d[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = sr.u[v * N + g];
+        if (sr.u_new) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) d[v] = sr.u_new[v * N + g] - u[v];
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            double s = 0.0;
+            for (int i = 0; i < sr.nst; ++i) s = fma(sr.coef[i], sr.k[i][v * N + g], s);
+            d[v] = s;
+          }
+        }
+        if (sr.d_out) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) sr.d_out[v * N + g] = d[v];
+        }
+        const double rho = u[0], ir = 1.0 / rho;
+        const double v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
+        const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
+        const double p = (gam - 1.0) * (u[4] - 0.5 * rho * v2s);
+        const double ip = 1.0 / p;
+        const double dv0 = (d[1] - v0 * d[0]) * ir, dv1 = (d[2] - v1 * d[0]) * ir, dv2 = (d[3] - v2 * d[0]) * ir;
+        const double Pn = mass_weight<P1>(P, n);
+        nd[r].X0 = d[0] * ir;
+        nd[r].Y0 = (gam - 1.0) * (d[4] - (v0 * d[1] + v1 * d[2] + v2 * d[3]) + 0.5 * v2s * d[0]) * ip;
+        nd[r].V2 = rho * (dv0 * dv0 + dv1 * dv1 + dv2 * dv2) * ip;
+        nd[r].c = Pn * rho;
+        const double XY = nd[r].X0 - nd[r].Y0;
+        a_part += 0.5 * nd[r].c * (nd[r].X0 * nd[r].X0 + XY * XY / (gam - 1.0) + nd[r].V2);
+        s_part += nd[r].c;
+        if (sr.u_new) {
+          // A = sum P w(u).d - d_eta with w = ((gam - s)/(gam-1) - beta|v|^2/2, beta v, -beta)
+          const double beta = rho * ip;
+          const double sp = log(p) - gam * log(rho);
+          const double w0 = (gam - sp) / (gam - 1.0) - 0.5 * beta * v2s;
+          A_part += Pn * (w0 * d[0] + beta * (v0 * d[1] + v1 * d[2] + v2 * d[3]) - beta * d[4]);
+        }
+      }
+    }
+    const double a = warp_sum(a_part);
+    const double ssum = warp_sum(s_part);
+    double A;
+    if (sr.u_new) A = warp_sum(A_part) - sr.deta[e];
+    else A = sr.A[e];
+    double gk = __longlong_as_double(0x7ff0000000000000LL);  // +inf: unconstrained
+    const double delta = sqrt(2.0 * a / ssum);
+    if (delta > sr.delta_floor) {
+      if (!(A < 0.0)) {
+        if (lane == 0) atomicOr(sr.status, kStatusNoRoot);
+      } else {
+        // Newton from the quadratic-model root, safeguarded by bisection on [lo, hi]
+        double lo = 0.0, hi = sr.gamma_max;
+        double rhi = 0.0;
+        bool phys_hi = true;
+        {
+          double sr_ = 0.0, sd_ = 0.0;
+          bool ok = true;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            double D, dD;
+            if (nd[r].c != 0.0) {
+              if (relax_node_eval(nd[r], hi, gam, D, dD)) {
+                sr_ += nd[r].c * D;
+                sd_ += nd[r].c * dD;
+              } else ok = false;
+            }
+          }
+          phys_hi = __all_sync(0xffffffffu, ok);
+          rhi = warp_sum(sr_) + hi * A;
+        }
+        if (phys_hi && !(rhi > 0.0)) {
+          gk = sr.gamma_max;
+        } else {
+          double gcur = fmin(fmax(-A / a, 1e-3), sr.gamma_max);
+          for (int it = 0; it < 200; ++it) {
+            double sr_ = 0.0, sd_ = 0.0;
+            bool ok = true;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              double D, dD;
+              if (nd[r].c != 0.0) {
+                if (relax_node_eval(nd[r], gcur, gam, D, dD)) {
+                  sr_ += nd[r].c * D;
+                  sd_ += nd[r].c * dD;
+                } else ok = false;
+              }
+            }
+            const bool phys = __all_sync(0xffffffffu, ok);
+            const double rv = warp_sum(sr_) + gcur * A;
+            const double dv = warp_sum(sd_) + A;
+            const bool pos = !phys || rv > 0.0;
+            if (pos) hi = gcur; else lo = gcur;
+            const double newton = gcur - rv / dv;
+            const bool nok = phys && isfinite(newton) && newton > lo && newton < hi;
+            const double nxt = nok ? newton : 0.5 * (lo + hi);
+            const double step = fabs(nxt - gcur);
+            const double tol = 8.881784197001252e-16 * fmax(1.0, gcur);  // 4 * 2^-52
+            const bool conv = (nok && step <= tol) || (hi - lo) <= tol || rv == 0.0;
+            if (conv) {
+              gk = nok ? nxt : gcur;
+              break;
+            }
+            gcur = nxt;
+          }
+        }
+      }
+    }
+    if (lane == 0) {
+      sr.gamma_elem[e] = gk;
+      atomic_min_positive(sr.gmin_bits, gk);
+    }
+  }
+}
+
+// eta_kappa = sum_n P_n S(q_n), S = -rho (ln p - gam ln rho)/(gam-1); one warp per element
+template <int P1>
+__global__ void k_entropy(Params P, const double* __restrict__ q, double* __restrict__ eta) {
+  constexpr int Np = P1 * P1 * P1;
+  const long long N = (long long)P.K * Np;
+  const double gam = P.gam;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < P.K; e += gridDim.x * wpb) {
+    double s = 0.0;
+    for (int n = lane; n < Np; n += 32) {
+      const long long g = (long long)e * Np + n;
+      const double rho = q[g];
+      const double ir = 1.0 / rho;
+      const double m0 = q[N + g], m1 = q[2 * N + g], m2 = q[3 * N + g];
+      const double p = (gam - 1.0) * (q[4 * N + g] - 0.5 * (m0 * m0 + m1 * m1 + m2 * m2) * ir);
+      s += mass_weight<P1>(P, n) * (-rho * (log(p) - gam * log(rho)) / (gam - 1.0));
+    }
+    s = warp_sum(s);
+    if (lane == 0) eta[e] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+template <int P1, typename TF>
+void Launcher<P1, TF>::prep(const Params& P, const StagePrep& sp, void* aux, int* status, cudaStream_t st,
+                            int grid) {
+  k_prep<TF><<<grid, 256, 0, st>>>(P, sp, static_cast<TF*>(aux), status);
+}
+
+template <int P1, typename TF>
+void Launcher<P1, TF>::face(const Params& P, const void* aux, void* F, cudaStream_t st, int grid) {
+  k_face<P1, TF><<<grid, 256, 0, st>>>(P, static_cast<const TF*>(aux), static_cast<TF*>(F));
+}
+
+template <int P1, typename TF>
+void Launcher<P1, TF>::grad(const Params& P, const void* aux, void* fV, cudaStream_t st, int grid) {
+  k_grad<P1, TF><<<grid, 256, 0, st>>>(P, static_cast<const TF*>(aux), static_cast<TF*>(fV));
+}
+
+template <int P1, typename TF>
+size_t Launcher<P1, TF>::volume_smem() {
+  constexpr int Np = P1 * P1 * P1;
+  return size_t(VolCfg<P1>::EPB) * Np * (12 * sizeof(TF) + 2 * sizeof(double));
+}
+
+template <int P1, typename TF>
+cudaError_t Launcher<P1, TF>::volume_setup() {
+  cudaError_t e1 = cudaFuncSetAttribute(k_volume<P1, TF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)volume_smem());
+  cudaError_t e2 = cudaFuncSetAttribute(k_volume<P1, TF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)volume_smem());
+  return e1 != cudaSuccess ? e1 : e2;
+}
+
+template <int P1, typename TF>
+void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* aux, const void* F, const void* fV,
+                              bool ns, cudaStream_t st) {
+  const int grid = (P.K + VolCfg<P1>::EPB - 1) / VolCfg<P1>::EPB;
+  if (ns)
+    k_volume<P1, TF, true><<<grid, VolCfg<P1>::THREADS, volume_smem(), st>>>(
+        P, sv, static_cast<const TF*>(aux), static_cast<const TF*>(F), static_cast<const TF*>(fV));
+  else
+    k_volume<P1, TF, false><<<grid, VolCfg<P1>::THREADS, volume_smem(), st>>>(
+        P, sv, static_cast<const TF*>(aux), static_cast<const TF*>(F), static_cast<const TF*>(fV));
+}
+
+template <int P1, typename TF>
+void Launcher<P1, TF>::relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid) {
+  k_relax<P1><<<grid, 128, 0, st>>>(P, sr);
+}
+
+template <int P1, typename TF>
+void Launcher<P1, TF>::entropy(const Params& P, const double* q, double* eta, cudaStream_t st, int grid) {
+  k_entropy<P1><<<grid, 128, 0, st>>>(P, q, eta);
+}
+
+}  // namespace es

@@ -1,0 +1,7 @@
+// Kernel instantiations for LGL degree p = 2 (P1 = 3 points per direction).
+#include "es_kernels.cuh"
+
+namespace es {
+template struct Launcher<3, double>;
+template struct Launcher<3, float>;
+}  // namespace es

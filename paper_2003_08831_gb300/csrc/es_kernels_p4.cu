@@ -1,0 +1,7 @@
+// Kernel instantiations for LGL degree p = 3 (P1 = 4 points per direction).
+#include "es_kernels.cuh"
+
+namespace es {
+template struct Launcher<4, double>;
+template struct Launcher<4, float>;
+}  // namespace es

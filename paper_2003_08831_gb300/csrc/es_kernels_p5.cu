@@ -1,0 +1,7 @@
+// Kernel instantiations for LGL degree p = 4 (P1 = 5 points per direction).
+#include "es_kernels.cuh"
+
+namespace es {
+template struct Launcher<5, double>;
+template struct Launcher<5, float>;
+}  // namespace es

@@ -1,0 +1,7 @@
+// Kernel instantiations for LGL degree p = 5 (P1 = 6 points per direction).
+#include "es_kernels.cuh"
+
+namespace es {
+template struct Launcher<6, double>;
+template struct Launcher<6, float>;
+}  // namespace es

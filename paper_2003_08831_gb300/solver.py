@@ -1,0 +1,105 @@
+"""Convenience layer over the C ABI: one context, torch device buffers, numpy host I/O.
+
+Argument marshalling and bookkeeping only; all arithmetic of the scheme runs in
+libes.so.  ``stable_dt`` is the harness' time-step rule (computed once from the
+initial state, then fixed).
+"""
+import numpy as np
+
+from . import _binding as B
+
+
+class Solver:
+    def __init__(self, p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0,
+                 interface_diss=1, relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64,
+                 delta_floor=1e-8, device="cuda"):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.p, self.n = int(p), tuple(int(a) for a in n)
+        self.lo, self.hi = tuple(map(float, lo)), tuple(map(float, hi))
+        self.gamma_gas, self.mu, self.Pr, self.R = gamma_gas, mu, Pr, R
+        self.P1 = self.p + 1
+        self.Np = self.P1 ** 3
+        self.K = self.n[0] * self.n[1] * self.n[2]
+        self.N = self.K * self.Np
+        self.cfg = B.make_config(p, n, lo, hi, gamma_gas, mu, Pr, R, interface_diss, relax, rk, precision,
+                                 delta_floor)
+        with torch.cuda.device(self.device):
+            self.ctx = B.es_create(self.cfg)
+
+    def close(self):
+        if self.ctx is not None:
+            B.es_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- buffers -------------------------------------------------------------------------
+    def empty_state(self):
+        return self.torch.empty((5, self.K, self.Np), dtype=self.torch.float64, device=self.device)
+
+    def to_device(self, q):
+        q = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(5, self.K, self.Np))
+        return self.torch.from_numpy(q).to(self.device)
+
+    def coords(self):
+        xyz = np.empty((3, self.K, self.Np))
+        B.es_node_coords(self.ctx, xyz)
+        return xyz
+
+    # -- C ABI calls -------------------------------------------------------------------------
+    def rhs(self, q, want_E=False, stream=None):
+        dq = self.empty_state()
+        E = self.torch.empty(self.K, dtype=self.torch.float64, device=self.device) if want_E else None
+        B.es_rhs(self.ctx, q, dq, E, stream)
+        return (dq, E) if want_E else dq
+
+    def entropy(self, q, stream=None):
+        eta = self.torch.empty(self.K, dtype=self.torch.float64, device=self.device)
+        B.es_entropy(self.ctx, q, eta, stream)
+        return eta
+
+    def relax_step(self, u_old, u_new, d_eta, stream=None):
+        gk = self.torch.empty(self.K, dtype=self.torch.float64, device=self.device)
+        g = self.torch.empty(1, dtype=self.torch.float64, device=self.device)
+        out = self.empty_state()
+        B.es_relax_step(self.ctx, u_old, u_new, d_eta, gk, g, out, stream)
+        return gk, g, out
+
+    def advance(self, q, nsteps, dt, t=None, want_hist=True, want_gamma_elem=True, stream=None):
+        torch = self.torch
+        if t is None:
+            t = torch.zeros(1, dtype=torch.float64, device=self.device)
+        hist = torch.empty(max(nsteps, 1), dtype=torch.float64, device=self.device) if want_hist else None
+        gk = torch.empty(self.K, dtype=torch.float64, device=self.device) if want_gamma_elem else None
+        B.es_advance(self.ctx, q, nsteps, dt, t, hist, gk, stream)
+        return t, hist, gk
+
+    def advance_host(self, q_host, nsteps, dt, t_host, hist_host=None, stream=None):
+        B.es_advance_host(self.ctx, q_host, nsteps, dt, t_host, hist_host, stream)
+
+    def status(self, stream=None):
+        return B.es_status(self.ctx, stream)
+
+    def launch_count(self):
+        return B.es_launch_count(self.ctx)
+
+
+def stable_dt(q, p, h, cfl, gamma_gas=1.4, mu=0.0, Pr=0.72):
+    """dt = cfl h_min/((2p+1) max(|v| + c)) (and the viscous limit); host-side harness rule."""
+    q = np.asarray(q).reshape(5, -1)
+    rho = q[0]
+    v = q[1:4] / rho
+    pr = (gamma_gas - 1.0) * (q[4] - 0.5 * rho * np.sum(v * v, axis=0))
+    lam = np.max(np.sqrt(np.sum(v * v, axis=0)) + np.sqrt(gamma_gas * pr / rho))
+    hmin = float(np.min(h))
+    dt = cfl * hmin / ((2 * p + 1) * lam)
+    if mu > 0.0:
+        hv = hmin / (2 * p + 1)
+        dt = min(dt, cfl * hv * hv * float(np.min(rho)) / (mu * max(4.0 / 3.0, gamma_gas / Pr)))
+    return dt
