@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Throughput of the locally relaxed entropy-stable RK step on GB300.
+
+Metric: DOF.RK-stage updates/s = LGL nodes x RK stages x steps / time, one
+"step" being one full relaxed RK step (every stage's right-hand side and the
+per-element gamma_kappa solve with the relaxed update) over the whole mesh.
+
+Default workload: 3D compressible Euler Taylor--Green vortex, Mach 0.1,
+periodic [0, 2 pi]^3, 32^3 hexahedra, p = 3 (2,097,152 nodes), BS3 (3 stages),
+local relaxation, CFL 0.5, FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own instance (independent
+problems, no data-path collective: weak scaling); rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on the host on a bounded sample of
+the same workload (rank 0 only).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+TWO_PI = 2.0 * math.pi
+METRIC = "DOF·RK-stage updates/s (RHS+local relaxation), FP64 vs mixed; % of roofline"
+UNIT = "DOF*stage/s"
+
+WORKLOADS = {
+    # the metric's configuration: Euler TGV 32^3 p=3 FP64, 200 steps
+    "tgv_euler_p3_32^3_fp64": dict(p=3, n=32, mu=0.0, precision=0, ic="tgv", steps=200),
+    "tgv_euler_p3_32^3_mixed": dict(p=3, n=32, mu=0.0, precision=1, ic="tgv", steps=200),
+    "tgv_ns_re1600_p4_32^3_fp64": dict(p=4, n=32, mu=1.0 / 1600.0, precision=0, ic="tgv", steps=200),
+    "tgv_ns_re1600_p4_32^3_mixed_noise": dict(p=4, n=32, mu=1.0 / 1600.0, precision=1, ic="tgv_noise", steps=200),
+    "vortex_euler_p3_4^3_fp64": dict(p=3, n=4, mu=0.0, precision=0, ic="vortex", steps=20),
+}
+MAIN = "tgv_euler_p3_32^3_fp64"
+STAGES = 3  # BS3: b_4 = 0
+
+
+# ---------------------------------------------------------------------------------------
+# algorithmic work of the volume kernel (the dominant one), counted from its source:
+# two-point flux 56 flops (FMA = 2, one division = 1), scatter to both nodes 20;
+# interface terms 20 per line; per-direction write-back 25 (p+1)^3 per element;
+# relaxation term (stages 2, 3) 12 per node; BR1 divergence 4 (2 (p+1)^2 + 8) per line.
+def volume_flops_per_element(p, ns=False, with_A=False):
+    P1 = p + 1
+    lines = 3 * P1 * P1
+    pairs = P1 * (P1 - 1) // 2
+    f = lines * (pairs * 76 + 20) + 25 * P1 ** 3
+    if with_A:
+        f += 12 * P1 ** 3
+    if ns:
+        f += lines * 4 * (2 * P1 * P1 + 8) + lines * 4 * P1
+    return f
+
+
+def fp_peak_tflops(precision, sm_mhz):
+    """ALU peak from unit counts x clock: 152 SMs, FP64 2 DFMA/clk/SM, FP32 128 FFMA/clk/SM."""
+    per_clk = 4.0 if precision == 0 else 256.0
+    return 152 * per_clk * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+def initial_state(solver, wl, gamma_gas=1.4):
+    from paper_2003_08831_gb300 import inputs
+    xyz = solver.coords()
+    x, y, z = xyz[0], xyz[1], xyz[2]
+    if wl["ic"] == "tgv":
+        return inputs.tgv_state(x, y, z, mach=0.1, gamma=gamma_gas)
+    if wl["ic"] == "tgv_noise":
+        return inputs.perturbed_tgv_state(x.reshape(-1), y.reshape(-1), z.reshape(-1), mach=0.1,
+                                          gamma=gamma_gas).reshape(5, solver.K, solver.Np)
+    return inputs.vortex_state(x, y, 0.0, centre=(5.0, 5.0))
+
+
+def make_solver(wl):
+    from paper_2003_08831_gb300.solver import Solver
+    n = wl["n"]
+    if wl["ic"] == "vortex":
+        lo, hi = (0.0, 0.0, 0.0), (10.0, 10.0, 10.0)
+    else:
+        lo, hi = (0.0, 0.0, 0.0), (TWO_PI, TWO_PI, TWO_PI)
+    return Solver(wl["p"], (n, n, n), lo, hi, mu=wl["mu"], Pr=0.72, precision=wl["precision"])
+
+
+def measure_device(wl, steps, warmup, dist=None, clocks_gpu=None):
+    """Device-resident timing of `steps` relaxed steps (CUDA events on the launching stream)."""
+    import torch
+    from paper_2003_08831_gb300.solver import stable_dt
+    s = make_solver(wl)
+    q0 = initial_state(s, wl)
+    h = [(s.hi[m] - s.lo[m]) / s.n[m] for m in range(3)]
+    dt = stable_dt(q0, s.p, h, 0.5, mu=wl["mu"])
+    q = s.to_device(q0)
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    s.advance(q, warmup, dt, t, want_hist=False, want_gamma_elem=False)
+    torch.cuda.synchronize()
+    rc = s.status()
+    if rc != 0:
+        raise RuntimeError("device status %d after warm-up" % rc)
+    hist = torch.empty(steps, dtype=torch.float64, device="cuda")
+    n0 = s.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(clocks_gpu).start() if clocks_gpu is not None else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    from paper_2003_08831_gb300 import _binding as B
+    B.es_advance(s.ctx, q, steps, dt, t, hist, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop() if sampler is not None else None
+    ms = e0.elapsed_time(e1)
+    launches = s.launch_count() - n0
+    rc = s.status()
+    if rc != 0:
+        raise RuntimeError("device status %d after the timed region" % rc)
+    g = hist.cpu().numpy()
+    res = {"ms": ms, "launches": launches, "dt": dt, "gamma_min": float(g.min()), "gamma_max": float(g.max()),
+           "nodes": s.N, "solver": s, "q": q, "t": t, "clocks": clocks}
+    return res
+
+
+def kernel_profile(res, steps):
+    """Second pass with per-launch CUDA events: time per kernel kind."""
+    import torch
+    s, q, t = res["solver"], res["q"], res["t"]
+    s.profile(True)
+    s.advance(q, steps, res["dt"], t, want_hist=False, want_gamma_elem=False)
+    torch.cuda.synchronize()
+    prof = s.profile_read()
+    s.profile(False)
+    return prof
+
+
+def measure_e2e(wl, steps, warmup):
+    """End to end through the C ABI on pinned HOST buffers: per step H2D of the state,
+    one relaxed step, D2H of the state, t and gamma (es_advance_host)."""
+    import torch
+    from paper_2003_08831_gb300.solver import stable_dt
+    s = make_solver(wl)
+    q0 = initial_state(s, wl)
+    h = [(s.hi[m] - s.lo[m]) / s.n[m] for m in range(3)]
+    dt = stable_dt(q0, s.p, h, 0.5, mu=wl["mu"])
+    qh = torch.from_numpy(np.ascontiguousarray(q0.reshape(5, -1))).pin_memory()
+    th = torch.zeros(1, dtype=torch.float64).pin_memory()
+    gh = torch.zeros(1, dtype=torch.float64).pin_memory()
+    qn, tn, gn = qh.numpy(), th.numpy(), gh.numpy()
+    for _ in range(warmup):
+        s.advance_host(qn, 1, dt, tn, gn)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.advance_host(qn, 1, dt, tn, gn)
+    el = time.perf_counter() - t0
+    if s.status() != 0:
+        raise RuntimeError("device status after e2e run")
+    nodes = s.N
+    s.close()
+    return {"value": nodes * STAGES * steps / el, "unit": UNIT,
+            "h2d_bytes_per_step": int(5 * nodes * 8 + 8), "d2h_bytes_per_step": int(5 * nodes * 8 + 16),
+            "ms_per_step": 1e3 * el / steps}
+
+
+# ---------------------------------------------------------------------------------------
+def oracle_sample(steps_or_seconds, by_time=True, ne=6):
+    """The FP64 CPU oracle on a periodic ne^3-element sub-box of the TGV workload (same p,
+    element size and state), full relaxed BS3 steps.  Returns (DOF*stage/s, steps, seconds)."""
+    from oracle import dg, rk
+    from paper_2003_08831_gb300 import inputs
+    p, N = 3, 32
+    h = TWO_PI / N
+    mesh = dg.Mesh(p, (ne, ne, ne), (0.0, 0.0, 0.0), (ne * h, ne * h, ne * h))
+    x, y, z = mesh.coords()
+    U = inputs.tgv_state(x, y, z, mach=0.1)
+    phys = dg.Physics(1.4, diss=1)
+    dt = rk.stable_dt(mesh, U, phys, 0.5)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        r = rk.rk_step(mesh, U, dt, phys, rk.BS3)
+        U = r.U
+        n += 1
+        el = time.perf_counter() - t0
+        if (by_time and el >= steps_or_seconds) or (not by_time and n >= steps_or_seconds):
+            break
+    nodes = mesh.K * mesh.Np
+    return nodes * STAGES * n / el, n, el, nodes
+
+
+def cpu_cores_used():
+    return 1  # numpy elementwise kernels run on one thread
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample(1, by_time=False)
+    value, n, el, nodes = oracle_sample(args.steps, by_time=False)
+    sample = "periodic 6^3-element sub-box (%d nodes) of the 32^3 p=3 Euler TGV, full relaxed BS3 steps" % nodes
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (closed-form TGV)",
+        "config": {"workload": MAIN, "oracle": "numpy FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=MAIN, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-forms", action="store_true", help="skip the extra precision/physics forms")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_full(args, rank, world, local_rank)
+
+
+def run_full(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    __graft_entry__.build()
+    wl = WORKLOADS[args.workload]
+    res = measure_device(wl, args.steps, args.warmup, dist=dist, clocks_gpu=local_rank)
+    ms = res["ms"]
+    if dist is not None:
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    clocks = res.pop("clocks", None)
+    nodes = res["nodes"]
+    value = world * nodes * STAGES * args.steps / (ms / 1e3)
+    prof = kernel_profile(res, min(args.steps, 50))
+    res["solver"].close()
+    del res["q"], res["t"], res["solver"]
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+        return 0
+    p = wl["p"]
+    K = wl["n"] ** 3
+    ns = wl["mu"] > 0
+    # average over the 3 stages: the A term is accumulated in stages 2 and 3
+    fl = K * (volume_flops_per_element(p, ns, False) + 2 * volume_flops_per_element(p, ns, True)) / 3.0
+    vol_ms, vol_n = prof["volume"]
+    avg_ms = vol_ms / max(vol_n, 1)
+    achieved = fl / (avg_ms * 1e-3) / 1e12
+    sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
+    peak = fp_peak_tflops(wl["precision"], sm_mhz)
+    tot = sum(v[0] for v in prof.values())
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["precision"] == 0 else "f64+f32",
+        "data": "synthetic (closed-form Taylor-Green vortex, Mach 0.1)",
+        "config": {"workload": args.workload, "elements": K, "p": p, "nodes": nodes, "rk": "BS3 (3 stages)",
+                   "relaxation": "local", "cfl": 0.5, "dt": res["dt"], "interface": "EC + Rusanov",
+                   "l2": "inputs larger than L2 (state + 3 stage buffers + aux > 500 MB), no flush",
+                   "gamma_range": [res["gamma_min"], res["gamma_max"]]},
+        "gpu_launches": int(res["launches"]),
+        "roofline": {"bound": "alu", "kernel": "k_volume (flux differencing + SATs)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "peak_source": "%s ALU peak from unit counts x median SM clock (%.0f MHz): 152 SMs x %s"
+                                    % ("FP64" if wl["precision"] == 0 else "FP32", sm_mhz,
+                                       "2 DFMA/clk" if wl["precision"] == 0 else "128 FFMA/clk"),
+                     "flops_per_launch": fl, "avg_launch_ms": avg_ms},
+        "kernel_share": {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1] > 0},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu:
+        v, n, el, nn = oracle_sample(10.0, by_time=True)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                               "sample": "periodic 6^3-element sub-box (%d nodes) of the workload's mesh and "
+                                         "state, %d full relaxed BS3 steps in %.1f s" % (nn, n, el)}
+    out["e2e"] = measure_e2e(wl, min(args.steps, 20), 3)
+    if world == 1 and not args.no_forms:
+        forms = {}
+        for name in ["tgv_euler_p3_32^3_mixed", "tgv_ns_re1600_p4_32^3_fp64", "tgv_ns_re1600_p4_32^3_mixed_noise"]:
+            w2 = WORKLOADS[name]
+            steps2 = 50
+            r2 = measure_device(w2, steps2, 3)
+            r2["solver"].close()
+            forms[name] = {"value": r2["nodes"] * STAGES * steps2 / (r2["ms"] / 1e3),
+                           "ms_per_step": r2["ms"] / steps2, "steps": steps2,
+                           "gamma_range": [r2["gamma_min"], r2["gamma_max"]], "launches": int(r2["launches"])}
+            del r2
+        out["forms"] = forms
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

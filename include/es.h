@@ -118,6 +118,22 @@ int es_status(es_ctx* ctx, void* stream);
 /* Number of kernel launches the context has enqueued since es_create. */
 long long es_launch_count(const es_ctx* ctx);
 
+/* Per-kernel timing (instrumentation, not part of the method).  While enabled,
+ * every launch of the context is bracketed by CUDA events recorded on the
+ * launching stream.  es_profile_read synchronises the device and returns,
+ * per kernel kind (ES_KERNEL_*), the summed event time in ms and the launch
+ * count since the last read, then resets them.  Arrays hold ES_KERNEL_COUNT
+ * entries. */
+#define ES_KERNEL_PREP 0    /* stage state + parameter vector */
+#define ES_KERNEL_FACE 1    /* interface fluxes */
+#define ES_KERNEL_GRAD 2    /* BR1 gradients + viscous flux */
+#define ES_KERNEL_VOLUME 3  /* flux differencing, SATs, viscous divergence */
+#define ES_KERNEL_RELAX 4   /* gamma_kappa root solve */
+#define ES_KERNEL_OTHER 5   /* scalar bookkeeping, final update, entropy */
+#define ES_KERNEL_COUNT 6
+int es_profile_enable(es_ctx* ctx, int enable);
+int es_profile_read(es_ctx* ctx, double* ms, long long* launches);
+
 /* Static message for an ES_* code. */
 const char* es_strerror(int code);
 

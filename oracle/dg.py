@@ -187,6 +187,37 @@ def rhs(mesh, U, phys):
     return out
 
 
+def rhs_term_magnitude(mesh, U, phys):
+    """Sum of the absolute values of the terms that rhs() adds at every node.
+
+    Test infrastructure: the rounding error of any FP64 evaluation of the
+    right-hand side is a small multiple of eps times this magnitude, which can
+    exceed |rhs| by orders of magnitude where the fluxes nearly cancel (low Mach
+    number: the pressure part of the momentum flux).
+    """
+    g = phys.gamma
+    p = mesh.p
+    T = np.zeros_like(U)
+    for m in range(3):
+        eax, nax = _AXES[m]
+        s = 2.0 / mesh.h[m]
+        A = np.moveaxis(U, nax, -1)
+        F = gas.ec_flux(A[..., :, None], A[..., None, :], g, m)
+        T += s * np.moveaxis(np.einsum("ij,...ij->...i", np.abs(2.0 * mesh.D), np.abs(F)), -1, nax)
+        q_right = _face(U, p, nax)
+        q_left = _face(U, 0, nax)
+        f_right = gas.interface_flux(q_right, np.roll(q_left, -1, axis=eax), g, m, phys.diss)
+        f_left = np.roll(f_right, 1, axis=eax)
+        _add_face(T, p, nax, s / mesh.omega[p] * (np.abs(f_right) + np.abs(gas.euler_flux(q_right, g, m))))
+        _add_face(T, 0, nax, s / mesh.omega[0] * (np.abs(f_left) + np.abs(gas.euler_flux(q_left, g, m))))
+    if phys.mu != 0.0:
+        _, theta, fv = viscous_term(mesh, U, phys, return_parts=True)
+        for m in range(3):
+            eax, nax = _AXES[m]
+            T += (2.0 / mesh.h[m]) * _apply_D(np.abs(mesh.D), np.abs(fv[m]), nax)
+    return T
+
+
 def local_entropies(mesh, U, phys):
     """eta_kappa(u) = 1^T P S_kappa (Section 3.2)."""
     return mesh.element_sum(gas.entropy(U, phys.gamma))

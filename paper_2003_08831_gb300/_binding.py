@@ -22,7 +22,9 @@ ES_FP64, ES_MIXED = 0, 1
 ES_RELAX_NONE, ES_RELAX_LOCAL = 0, 1
 
 EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "es_advance",
-           "es_advance_host", "es_node_coords", "es_status", "es_launch_count", "es_strerror"]
+           "es_advance_host", "es_node_coords", "es_status", "es_launch_count", "es_strerror",
+           "es_profile_enable", "es_profile_read"]
+KERNEL_KINDS = ["prep", "face", "grad", "volume", "relax", "other"]
 
 
 class es_config(ctypes.Structure):
@@ -72,6 +74,10 @@ def load(path=None):
     lib.es_status.restype = i
     lib.es_launch_count.argtypes = [vp]
     lib.es_launch_count.restype = ctypes.c_longlong
+    lib.es_profile_enable.argtypes = [vp, i]
+    lib.es_profile_enable.restype = i
+    lib.es_profile_read.argtypes = [vp, vp, vp]
+    lib.es_profile_read.restype = i
     lib.es_strerror.argtypes = [i]
     lib.es_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -176,3 +182,16 @@ def es_launch_count(ctx):
 
 def es_strerror(code):
     return strerror(code)
+
+
+def es_profile_enable(ctx, enable):
+    _check(load().es_profile_enable(ctx, int(bool(enable))), "es_profile_enable")
+
+
+def es_profile_read(ctx):
+    """{kind: (ms, launches)} since the last read."""
+    import numpy as np
+    ms = np.zeros(len(KERNEL_KINDS))
+    n = np.zeros(len(KERNEL_KINDS), dtype=np.int64)
+    _check(load().es_profile_read(ctx, _ptr(ms), _ptr(n)), "es_profile_read")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}

@@ -136,6 +136,13 @@ struct es_ctx {
   double* hist_host_dev = nullptr;
   int hist_cap = 0;
   long long launches = 0;
+  // per-kernel event timing (es_profile_enable)
+  bool profiling = false;
+  struct Mark { int kind; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[ES_KERNEL_COUNT] = {0};
+  long long prof_n[ES_KERNEL_COUNT] = {0};
 };
 
 namespace {
@@ -179,6 +186,11 @@ int dev_alloc(T** p, size_t count) {
 
 void free_ctx(es_ctx* c) {
   if (!c) return;
+  for (auto& m : c->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
   for (auto& p : c->k) cudaFree(p);
   cudaFree(c->aux);
   cudaFree(c->F);
@@ -196,21 +208,61 @@ void free_ctx(es_ctx* c) {
   delete c;
 }
 
+cudaEvent_t take_event(es_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Folds recorded event pairs into the per-kind totals (synchronises the device).
+void flush_marks(es_ctx* c) {
+  if (c->marks.empty()) return;
+  cudaDeviceSynchronize();
+  for (auto& m : c->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+      c->prof_ms[m.kind] += ms;
+      c->prof_n[m.kind] += 1;
+    }
+    c->pool.push_back(m.a);
+    c->pool.push_back(m.b);
+  }
+  c->marks.clear();
+  cudaGetLastError();
+}
+
+// Brackets one launch with events when profiling is on.
+template <typename Fn>
+void timed(es_ctx* c, int kind, cudaStream_t st, Fn&& fn) {
+  c->launches += 1;
+  if (!c->profiling) {
+    fn();
+    return;
+  }
+  if (c->marks.size() >= 4096) flush_marks(c);
+  es_ctx::Mark m{kind, take_event(c), take_event(c)};
+  cudaEventRecord(m.a, st);
+  fn();
+  cudaEventRecord(m.b, st);
+  c->marks.push_back(m);
+}
+
 // One stage's right-hand side into kout (+ element sums), on state
 // u (+ update) + sum_j coef[j] k[j].
 int run_stage(es_ctx* c, const StagePrep& sp, const StageVol& sv, cudaStream_t st) {
   const bool ns = c->cfg.mu != 0.0;
   return dispatch(c, [&](auto L) {
     using Lc = decltype(L);
-    Lc::prep(c->P, sp, c->aux, c->status, st, grid_for(c, c->N, 256));
-    Lc::face(c->P, c->aux, c->F, st, grid_for(c, 3LL * c->K * c->P1 * c->P1, 256));
-    c->launches += 2;
-    if (ns) {
-      Lc::grad(c->P, c->aux, c->fV, st, grid_for(c, c->N, 256));
-      c->launches += 1;
-    }
-    Lc::volume(c->P, sv, c->aux, c->F, c->fV, ns, st);
-    c->launches += 1;
+    timed(c, ES_KERNEL_PREP, st, [&] { Lc::prep(c->P, sp, c->aux, c->status, st, grid_for(c, c->N, 256)); });
+    timed(c, ES_KERNEL_FACE, st,
+          [&] { Lc::face(c->P, c->aux, c->F, st, grid_for(c, 3LL * c->K * c->P1 * c->P1, 256)); });
+    if (ns) timed(c, ES_KERNEL_GRAD, st, [&] { Lc::grad(c->P, c->aux, c->fV, st, grid_for(c, c->N, 256)); });
+    timed(c, ES_KERNEL_VOLUME, st, [&] { Lc::volume(c->P, sv, c->aux, c->F, c->fV, ns, st); });
     return last_launch_error();
   });
 }
@@ -218,8 +270,7 @@ int run_stage(es_ctx* c, const StagePrep& sp, const StageVol& sv, cudaStream_t s
 int run_relax(es_ctx* c, const StageRelax& sr, cudaStream_t st) {
   const int grid = (int)std::min<long long>((c->K + 3) / 4, (long long)c->sm_count * 16);
   return dispatch(c, [&](auto L) {
-    decltype(L)::relax(c->P, sr, st, grid);
-    c->launches += 1;
+    timed(c, ES_KERNEL_RELAX, st, [&] { decltype(L)::relax(c->P, sr, st, grid); });
     return last_launch_error();
   });
 }
@@ -241,8 +292,7 @@ int advance_device(es_ctx* c, double* q, int nsteps, double dt, double* t, doubl
   const Tableau& T = c->tab;
   const bool relax = c->cfg.relax == ES_RELAX_LOCAL;
   int rc = ES_OK;
-  launch_reset_min(c->gmin, st);
-  c->launches += 1;
+  timed(c, ES_KERNEL_OTHER, st, [&] { launch_reset_min(c->gmin, st); });
   for (int n = 0; n < nsteps && rc == ES_OK; ++n) {
     for (int i = 0; i < T.s && rc == ES_OK; ++i) {
       StagePrep sp;
@@ -264,6 +314,17 @@ int advance_device(es_ctx* c, double* q, int nsteps, double dt, double* t, doubl
       StageVol sv;
       std::memset(&sv, 0, sizeof(sv));
       sv.kout = c->k[i];
+      if (i == T.s - 1) {  // last stage: write d = dt sum_j b_j k_j instead of k_s
+        sv.d_out = c->d;
+        sv.dcoef_self = dt * T.b[i];
+        for (int j = 0; j < i; ++j) {
+          if (T.b[j] != 0.0) {
+            sv.dcoef[sv.nd] = dt * T.b[j];
+            sv.dk[sv.nd] = c->k[j];
+            sv.nd++;
+          }
+        }
+      }
       sv.dw = want_dw ? c->dw : nullptr;
       sv.A = relax ? c->A : nullptr;
       sv.A_scale = -dt * T.b[i];
@@ -273,25 +334,20 @@ int advance_device(es_ctx* c, double* q, int nsteps, double dt, double* t, doubl
     if (rc != ES_OK) break;
     StageRelax sr = relax_base(c);
     sr.u = q;
-    sr.nst = T.s;
-    for (int i = 0; i < T.s; ++i) {
-      sr.coef[i] = dt * T.b[i];
-      sr.k[i] = c->k[i];
-    }
+    sr.d_in = c->d;
     sr.A = c->A;
-    sr.d_out = c->d;
     if (!relax) sr.delta_floor = INFINITY;  // combine only: every element unconstrained
     rc = run_relax(c, sr, st);
     if (rc != ES_OK) break;
-    launch_scalar(c->gmin, c->scal, t ? t : c->scal + 1, hist, n, dt, relax ? 1 : 0, st);
-    c->launches += 1;
+    timed(c, ES_KERNEL_OTHER, st,
+          [&] { launch_scalar(c->gmin, c->scal, t ? t : c->scal + 1, hist, n, dt, relax ? 1 : 0, st); });
     if (gamma_elem_out && n == nsteps - 1)
       rc = cuda_check(cudaMemcpyAsync(gamma_elem_out, c->gamma_elem, sizeof(double) * c->K,
                                       cudaMemcpyDeviceToDevice, st));
   }
   if (rc == ES_OK && nsteps > 0) {
-    launch_update(q, q, c->d, c->scal, 5 * c->N, st, grid_for(c, 5 * c->N, 256));
-    c->launches += 1;
+    timed(c, ES_KERNEL_OTHER, st,
+          [&] { launch_update(q, q, c->d, c->scal, 5 * c->N, st, grid_for(c, 5 * c->N, 256)); });
     rc = last_launch_error();
   }
   return rc;
@@ -368,7 +424,7 @@ int es_create(const es_config* cfg, es_ctx** out) {
   const long long P2 = (long long)c->P1 * c->P1;
   int rc = ES_OK;
   for (int i = 0; i < c->tab.s && rc == ES_OK; ++i) rc = dev_alloc(&c->k[i], 5 * N);
-  if (rc == ES_OK) rc = cuda_check(cudaMalloc(&c->aux, 7 * N * c->tf)) == ES_OK ? ES_OK : ES_ERR_NOMEM;
+  if (rc == ES_OK) rc = cuda_check(cudaMalloc(&c->aux, kAux * N * c->tf)) == ES_OK ? ES_OK : ES_ERR_NOMEM;
   if (rc == ES_OK) rc = cuda_check(cudaMalloc(&c->F, 15 * K * P2 * c->tf)) == ES_OK ? ES_OK : ES_ERR_NOMEM;
   if (rc == ES_OK && C.mu > 0.0) rc = cuda_check(cudaMalloc(&c->fV, 12 * N * c->tf)) == ES_OK ? ES_OK : ES_ERR_NOMEM;
   if (rc == ES_OK) rc = dev_alloc(&c->dw, 5 * N);
@@ -414,8 +470,7 @@ int es_entropy(es_ctx* c, const double* q, double* eta, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int grid = (int)std::min<long long>((c->K + 3) / 4, (long long)c->sm_count * 16);
   return dispatch(c, [&](auto L) {
-    decltype(L)::entropy(c->P, q, eta, st, grid);
-    c->launches += 1;
+    timed(c, ES_KERNEL_OTHER, st, [&] { decltype(L)::entropy(c->P, q, eta, st, grid); });
     return last_launch_error();
   });
 }
@@ -424,8 +479,7 @@ int es_relax_step(es_ctx* c, const double* u_old, const double* u_new, const dou
                   double* gamma, double* u_out, void* stream) {
   if (!c || !u_old || !u_new || !d_eta || !u_out || u_out == u_old) return ES_ERR_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  launch_reset_min(c->gmin, st);
-  c->launches += 1;
+  timed(c, ES_KERNEL_OTHER, st, [&] { launch_reset_min(c->gmin, st); });
   StageRelax sr = relax_base(c);
   sr.u = u_old;
   sr.u_new = u_new;
@@ -433,10 +487,9 @@ int es_relax_step(es_ctx* c, const double* u_old, const double* u_new, const dou
   sr.d_out = c->d;
   int rc = run_relax(c, sr, st);
   if (rc != ES_OK) return rc;
-  launch_scalar(c->gmin, c->scal, c->scal + 1, nullptr, 0, 0.0, 1, st);
-  c->launches += 1;
-  launch_update(u_out, u_old, c->d, c->scal, 5 * c->N, st, grid_for(c, 5 * c->N, 256));
-  c->launches += 1;
+  timed(c, ES_KERNEL_OTHER, st, [&] { launch_scalar(c->gmin, c->scal, c->scal + 1, nullptr, 0, 0.0, 1, st); });
+  timed(c, ES_KERNEL_OTHER, st,
+        [&] { launch_update(u_out, u_old, c->d, c->scal, 5 * c->N, st, grid_for(c, 5 * c->N, 256)); });
   rc = last_launch_error();
   if (rc != ES_OK) return rc;
   if (gamma_elem) {
@@ -520,6 +573,25 @@ int es_status(es_ctx* c, void* stream) {
 }
 
 long long es_launch_count(const es_ctx* c) { return c ? c->launches : 0; }
+
+int es_profile_enable(es_ctx* c, int enable) {
+  if (!c) return ES_ERR_INVALID;
+  if (!enable) flush_marks(c);
+  c->profiling = enable != 0;
+  return ES_OK;
+}
+
+int es_profile_read(es_ctx* c, double* ms, long long* launches) {
+  if (!c || !ms || !launches) return ES_ERR_INVALID;
+  flush_marks(c);
+  for (int k = 0; k < ES_KERNEL_COUNT; ++k) {
+    ms[k] = c->prof_ms[k];
+    launches[k] = c->prof_n[k];
+    c->prof_ms[k] = 0.0;
+    c->prof_n[k] = 0;
+  }
+  return ES_OK;
+}
 
 const char* es_strerror(int code) {
   switch (code) {

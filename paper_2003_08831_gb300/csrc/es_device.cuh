@@ -57,19 +57,18 @@ __device__ __forceinline__ double mass_weight(const Params& P, int n) {
 }
 
 // ---------------------------------------------------------------------------
-// Parameter-vector state used by the two-point flux: z = sqrt(rho/p) (1, v, p)
-// plus ln z1 and ln z5.  Layout of the 7 values: z1, z2, z3, z4, z5, lz1, lz5.
+// Parameter-vector state used by the two-point flux: z = sqrt(rho/p) (1, v, p).
+constexpr int kAux = 5;
 template <typename T>
 struct Zstate {
   T z[5];
-  T lz1, lz5;
 };
 
 // Series logarithmic-mean pieces.  For aL, aR > 0 with s = aL + aR,
 // d = aL - aR and u = (d/s)^2:  ln-mean = (s/2) / F(u) with
 // F(u) = atanh(sqrt u)/sqrt u = 1 + u/3 + u^2/5 + u^3/7 + ...  Below the
 // threshold both F and 1/F are taken from their Taylor series (truncation
-// below the type's rounding); above it the mean is d / (ln aL - ln aR).
+// below the type's rounding); above it the mean is d / ln(aL/aR).
 template <typename T> struct LogMeanConst;
 template <> struct LogMeanConst<double> { static constexpr double eps = 1.0e-4; };
 template <> struct LogMeanConst<float> { static constexpr float eps = 1.0e-2f; };
@@ -114,9 +113,9 @@ __device__ __forceinline__ void ec_flux(const Zstate<T>& a, const Zstate<T>& b, 
   // 1 / ln-mean(z1) and ln-mean(z5)
   T inv_lm1, lm5;
   if (u1 < eps) inv_lm1 = T(2) * series_F(u1) * inv1;
-  else inv_lm1 = (a.lz1 - b.lz1) / D1;
+  else inv_lm1 = log(a.z[0] / b.z[0]) / D1;
   if (u5 < eps) lm5 = T(0.5) * S5 * series_invF(u5);
-  else lm5 = D5 / (a.lz5 - b.lz5);
+  else lm5 = D5 / log(a.z[4] / b.z[4]);
   const T zb1 = T(0.5) * S1;
   const T rho_hat = zb1 * lm5;
   const T u0 = (a.z[1] + b.z[1]) * inv1;
@@ -155,23 +154,39 @@ __device__ __forceinline__ void z_to_q(const Zstate<T>& s, const FluxConst<T>& C
 
 // Entropy variables from the parameter vector:
 // w = ((gam - s)/(gam-1) - |zv|^2/2, z1 zv, -z1^2), s = -(gam+1) ln z1 - (gam-1) ln z5.
+// w_2..w_5 need no logarithm (the viscous terms use only those).
+template <typename T>
+__device__ __forceinline__ void z_to_wv(const Zstate<T>& s, T w[4]) {
+  w[0] = s.z[0] * s.z[1];
+  w[1] = s.z[0] * s.z[2];
+  w[2] = s.z[0] * s.z[3];
+  w[3] = -s.z[0] * s.z[0];
+}
 template <typename T>
 __device__ __forceinline__ void z_to_w(const Zstate<T>& s, const FluxConst<T>& C, T w[5]) {
-  const T sp = -(C.gam + T(1)) * s.lz1 - (C.gam - T(1)) * s.lz5;
+  const T sp = -(C.gam + T(1)) * log(s.z[0]) - (C.gam - T(1)) * log(s.z[4]);
   w[0] = (C.gam - sp) * C.inv_gm1 - T(0.5) * (s.z[1] * s.z[1] + s.z[2] * s.z[2] + s.z[3] * s.z[3]);
-  w[1] = s.z[0] * s.z[1];
-  w[2] = s.z[0] * s.z[2];
-  w[3] = s.z[0] * s.z[3];
-  w[4] = -s.z[0] * s.z[0];
+  z_to_wv(s, w + 1);
 }
 
 // ---------------------------------------------------------------------------
-// log(1 + z) - z without cancellation.  For |z| <= 0.1: with t = z/(2+z),
-// log1p(z) = 2 atanh(t) = 2 (t + t^3/3 + t^5/5 + ...) and z = 2t/(1-t), so
-// log1p(z) - z = -t z + 2 t^3 (1/3 + t^2/5 + t^4/7 + ...); |t| < 0.053 and
-// seven terms of the even series reach 1e-17 relative.  Otherwise the direct
-// difference, whose cancellation costs at most a factor 20 in relative error.
+// log(1 + z) - z without cancellation.
+// |z| <= 1e-3: Taylor series -z^2/2 + z^3/3 - ... + z^7/7 (the first omitted
+//   term is below 2.5e-19 of the result).
+// |z| <= 0.1: with t = z/(2+z), log1p(z) = 2 atanh(t) = 2 (t + t^3/3 + ...) and
+//   z = 2t/(1-t), so log1p(z) - z = -t z + 2 t^3 (1/3 + t^2/5 + t^4/7 + ...);
+//   |t| < 0.053 and eight terms of the even series reach 1e-17 relative.
+// otherwise the direct difference (cancellation costs at most a factor 20).
 __device__ __forceinline__ double log1pmx(double z) {
+  if (fabs(z) <= 1e-3) {
+    double s = 1.0 / 7.0;
+    s = fma(s, z, -1.0 / 6.0);
+    s = fma(s, z, 1.0 / 5.0);
+    s = fma(s, z, -1.0 / 4.0);
+    s = fma(s, z, 1.0 / 3.0);
+    s = fma(s, z, -0.5);
+    return z * z * s;
+  }
   if (fabs(z) <= 0.1) {
     const double t = z / (2.0 + z);
     const double t2 = t * t;
@@ -200,22 +215,29 @@ struct RelaxNode {
 //   phi(x) = (1+x) log1p(x) - x, psi(y) = y - log1p(y);
 //   d/dg (D/rho) = [X0 (gam log1p(x) - log1p(y)) + y' (y - x)/(1+y)]/(gam-1) + K',
 //   K' = g V2/(1+x) (1 - x/(2(1+x))), y' = Y0 - (gam-1) K'.
+// One division serves 1/(1+x) and 1/(1+y): with Yb = g Y0 (1+x) - (gam-1) g^2 V2/2,
+// y = Yb/(1+x) and 1+y = (1+x+Yb)/(1+x).
 // Returns false if the state at gamma is not physical (1+x <= 0 or 1+y <= 0).
-__device__ __forceinline__ bool relax_node_eval(const RelaxNode& nd, double g, double gam, double& D,
-                                                double& dD) {
+__device__ __forceinline__ bool relax_node_eval(const RelaxNode& nd, double g, double gam, double inv_gm1,
+                                                double& D, double& dD) {
   const double x = g * nd.X0;
-  if (!(x > -1.0)) return false;
-  const double q = 1.0 / (1.0 + x);
-  const double K = 0.5 * g * g * nd.V2 * q;
-  const double y = g * nd.Y0 - (gam - 1.0) * K;
-  if (!(y > -1.0)) return false;
+  const double opx = 1.0 + x;
+  const double K0 = 0.5 * g * g * nd.V2;
+  const double Yb = g * nd.Y0 * opx - (gam - 1.0) * K0;
+  const double opy_n = opx + Yb;  // (1+y)(1+x)
+  if (!(opx > 0.0) || !(opy_n > 0.0)) return false;
+  const double inv = 1.0 / (opx * opy_n);
+  const double q = opy_n * inv;        // 1/(1+x)
+  const double iy = opx * opx * inv;   // 1/(1+y)
+  const double y = Yb * q;
+  const double K = K0 * q;
   const double Lx = log1pmx(x), Ly = log1pmx(y);
   const double l1px = x + Lx, l1py = y + Ly;
-  const double phi = (1.0 + x) * Lx + x * x;
-  D = (gam * phi - Ly - x * l1py) / (gam - 1.0) + K;
+  const double phi = opx * Lx + x * x;
+  D = (gam * phi - Ly - x * l1py) * inv_gm1 + K;
   const double dK = g * nd.V2 * q * (1.0 - 0.5 * x * q);
   const double dy = nd.Y0 - (gam - 1.0) * dK;
-  dD = (nd.X0 * (gam * l1px - l1py) + dy * (y - x) / (1.0 + y)) / (gam - 1.0) + dK;
+  dD = (nd.X0 * (gam * l1px - l1py) + dy * (y - x) * iy) * inv_gm1 + dK;
   return true;
 }
 

@@ -37,27 +37,29 @@ template <> struct VolCfg<6> { static constexpr int EPB = 4, THREADS = 160; };
 // beta = rho/p, ds = log1p(y) - gam log1p(x),
 // dw1 = -ds/(gam-1) - beta[(x-y)|v|^2 + (1+x)(2 v.dv + |dv|^2)]/(2(1+y)),
 // dw_v = beta[(x-y) v + (1+x) dv]/(1+y), dw5 = -beta (x-y)/(1+y).
+// With Pr = rho p = (gam-1)(rho E - |m|^2/2), one division 1/(rho rho' Pr) gives
+// 1/rho, 1/rho' and 1/p; a second gives 1/(1+y).
 __device__ __forceinline__ void entropy_var_increment(const double u[5], const double e[5], double gam,
-                                                      double dw[5]) {
+                                                      double inv_gm1, double dw[5]) {
   const double rho = u[0];
-  const double ir = 1.0 / rho;
+  const double rho1 = rho + e[0];
+  const double m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+  const double Pr = (gam - 1.0) * (rho * u[4] - 0.5 * m2);
+  const double inv = 1.0 / (rho * rho1 * Pr);
+  const double ir = rho1 * Pr * inv, ir1 = rho * Pr * inv, ip = rho * rho * rho1 * inv;
   const double v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
   const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
-  const double p = (gam - 1.0) * (u[4] - 0.5 * rho * v2s);
   const double x = e[0] * ir;
-  const double rho1 = rho + e[0];
-  const double ir1 = 1.0 / rho1;
   const double d0 = (e[1] - v0 * e[0]) * ir1, d1 = (e[2] - v1 * e[0]) * ir1, d2 = (e[3] - v2 * e[0]) * ir1;
   const double dv2 = d0 * d0 + d1 * d1 + d2 * d2;
-  const double ip = 1.0 / p;
   const double y =
       (gam - 1.0) * (e[4] - (v0 * e[1] + v1 * e[2] + v2 * e[3]) + 0.5 * v2s * e[0] - 0.5 * rho1 * dv2) * ip;
   const double beta = rho * ip;
   const double iy = 1.0 / (1.0 + y);
-  const double ds = log1p(y) - gam * log1p(x);
+  const double ds = (y + log1pmx(y)) - gam * (x + log1pmx(x));
   const double xy = x - y;
   const double dkin = 0.5 * beta * (xy * v2s + (1.0 + x) * (2.0 * (v0 * d0 + v1 * d1 + v2 * d2) + dv2)) * iy;
-  dw[0] = -ds / (gam - 1.0) - dkin;
+  dw[0] = -ds * inv_gm1 - dkin;
   dw[1] = beta * (xy * v0 + (1.0 + x) * d0) * iy;
   dw[2] = beta * (xy * v1 + (1.0 + x) * d1) * iy;
   dw[3] = beta * (xy * v2 + (1.0 + x) * d2) * iy;
@@ -94,33 +96,30 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
     const double v0 = y[1] * ir, v1 = y[2] * ir, v2 = y[3] * ir;
     const double p = (gam - 1.0) * (y[4] - 0.5 * rho * (v0 * v0 + v1 * v1 + v2 * v2));
     if (!(rho > 0.0) || !(p > 0.0)) atomicOr(status, kStatusNonphysical);
+    // z1 = sqrt(rho/p) = rho / sqrt(rho p), z5 = sqrt(rho p)
     if constexpr (sizeof(TF) == 8) {
-      const double z1 = sqrt(rho / p);
-      const double lr = log(rho), lp = log(p);
+      const double rs = rsqrt(rho * p);
+      const double z1 = rho * rs;
       aux[0 * N + g] = z1;
       aux[1 * N + g] = z1 * v0;
       aux[2 * N + g] = z1 * v1;
       aux[3 * N + g] = z1 * v2;
-      aux[4 * N + g] = rho / z1;       // sqrt(rho p)
-      aux[5 * N + g] = 0.5 * (lr - lp);
-      aux[6 * N + g] = 0.5 * (lr + lp);
+      aux[4 * N + g] = rho * p * rs;
     } else {
       const float rf = float(rho), pf = float(p);
-      const float z1 = sqrtf(rf / pf);
-      const float lr = logf(rf), lp = logf(pf);
+      const float rs = rsqrtf(rf * pf);
+      const float z1 = rf * rs;
       aux[0 * N + g] = z1;
       aux[1 * N + g] = z1 * float(v0);
       aux[2 * N + g] = z1 * float(v1);
       aux[3 * N + g] = z1 * float(v2);
-      aux[4 * N + g] = rf / z1;
-      aux[5 * N + g] = 0.5f * (lr - lp);
-      aux[6 * N + g] = 0.5f * (lr + lp);
+      aux[4 * N + g] = rf * pf * rs;
     }
     if (sp.dw) {
       double e[5], dw[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) e[v] = y[v] - u[v];
-      entropy_var_increment(u, e, gam, dw);
+      entropy_var_increment(u, e, gam, 1.0 / (gam - 1.0), dw);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sp.dw[v * N + g] = dw[v];
     }
@@ -132,9 +131,7 @@ template <int P1, typename TF>
 __device__ __forceinline__ Zstate<TF> load_z(const TF* __restrict__ aux, long long N, long long g) {
   Zstate<TF> s;
 #pragma unroll
-  for (int c = 0; c < 5; ++c) s.z[c] = aux[c * N + g];
-  s.lz1 = aux[5 * N + g];
-  s.lz5 = aux[6 * N + g];
+  for (int c = 0; c < kAux; ++c) s.z[c] = aux[c * N + g];
   return s;
 }
 
@@ -175,7 +172,6 @@ template <int P1, typename TF>
 __global__ void k_grad(Params P, const TF* __restrict__ aux, TF* __restrict__ fV) {
   constexpr int P2 = P1 * P1, Np = P1 * P2;
   const long long N = (long long)P.K * Np;
-  const FluxConst<TF> C = FluxConst<TF>::make(P.gam);
   const TF mu = TF(P.mu), kap = TF(P.kappa_heat), Rg = TF(P.R);
   const TF iw = TF(P.inv_omega_end);
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
@@ -191,23 +187,23 @@ __global__ void k_grad(Params P, const TF* __restrict__ aux, TF* __restrict__ fV
 #pragma unroll
       for (int j = 0; j < P1; ++j) {
         const Zstate<TF> s = load_z<P1, TF>(aux, N, (long long)e * Np + line_node<P1>(m, a, b, j));
-        TF w[5];
-        z_to_w(s, C, w);
+        TF w[4];
+        z_to_wv(s, w);
         const TF Dij = TF(P.D[im * P1 + j]);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] += Dij * w[1 + c];
+        for (int c = 0; c < 4; ++c) acc[c] += Dij * w[c];
       }
       if (im == P1 - 1 || im == 0) {
         const bool right = (im == P1 - 1);
         const int en = neighbour(P, e, m, right ? +1 : -1);
         const Zstate<TF> sn = load_z<P1, TF>(aux, N, (long long)en * Np + line_node<P1>(m, a, b, right ? 0 : P1 - 1));
         const Zstate<TF> ss = load_z<P1, TF>(aux, N, g);
-        TF wn[5], ws[5];
-        z_to_w(sn, C, wn);
-        z_to_w(ss, C, ws);
+        TF wn[4], ws[4];
+        z_to_wv(sn, wn);
+        z_to_wv(ss, ws);
         const TF sg = right ? TF(0.5) * iw : TF(-0.5) * iw;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] += sg * (wn[1 + c] - ws[1 + c]);
+        for (int c = 0; c < 4; ++c) acc[c] += sg * (wn[c] - ws[c]);
       }
       const TF met = TF(P.metric[m]);
 #pragma unroll
@@ -250,8 +246,8 @@ __global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageV
   constexpr int P2 = P1 * P1, Np = P1 * P2;
   constexpr int EPB = VolCfg<P1>::EPB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TF* za = reinterpret_cast<TF*>(smem_raw);            // [7][EPB*Np]
-  TF* acc = za + 7 * EPB * Np;                          // [5][EPB*Np]
+  TF* za = reinterpret_cast<TF*>(smem_raw);            // [kAux][EPB*Np]
+  TF* acc = za + kAux * EPB * Np;                       // [5][EPB*Np]
   double* red = reinterpret_cast<double*>(acc + 5 * EPB * Np);  // [2][EPB*Np]
   const long long N = (long long)P.K * Np;
   const int e0 = blockIdx.x * EPB;
@@ -262,7 +258,7 @@ __global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageV
 
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
 #pragma unroll
-    for (int c = 0; c < 7; ++c) za[c * EPB * Np + t] = aux[c * N + (long long)e0 * Np + t];
+    for (int c = 0; c < kAux; ++c) za[c * EPB * Np + t] = aux[c * N + (long long)e0 * Np + t];
   }
   __syncthreads();
 
@@ -278,9 +274,7 @@ __global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageV
       for (int i = 0; i < P1; ++i) {
         const int n = el * Np + line_node<P1>(m, a, b, i);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) z[i].z[c] = za[c * EPB * Np + n];
-        z[i].lz1 = za[5 * EPB * Np + n];
-        z[i].lz5 = za[6 * EPB * Np + n];
+        for (int c = 0; c < kAux; ++c) z[i].z[c] = za[c * EPB * Np + n];
       }
       TF r[P1][5];
 #pragma unroll
@@ -343,7 +337,7 @@ __global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageV
     __syncthreads();
   }
 
-  // node phase: write k_i, element sums
+  // node phase: write k_i (or, in the last stage, d = sum_j c_j k_j + c_self k_i), element sums
   const bool wantE = sv.E != nullptr;
   const bool wantA = sv.dw != nullptr;
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
@@ -351,17 +345,23 @@ __global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageV
     const int n = t % Np;
     double k[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      k[v] = double(acc[v * EPB * Np + t]);
-      sv.kout[v * N + g] = k[v];
+    for (int v = 0; v < 5; ++v) k[v] = double(acc[v * EPB * Np + t]);
+    if (sv.d_out) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double dv = sv.dcoef_self * k[v];
+        for (int j = 0; j < sv.nd; ++j) dv = fma(sv.dcoef[j], sv.dk[j][v * N + g], dv);
+        sv.d_out[v * N + g] = dv;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sv.kout[v * N + g] = k[v];
     }
     const double Pn = mass_weight<P1>(P, n);
     if (wantE) {
       Zstate<TF> s;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) s.z[c] = za[c * EPB * Np + t];
-      s.lz1 = za[5 * EPB * Np + t];
-      s.lz5 = za[6 * EPB * Np + t];
+      for (int c = 0; c < kAux; ++c) s.z[c] = za[c * EPB * Np + t];
       TF w[5];
       z_to_w(s, C, w);
       double sum = 0.0;
@@ -401,12 +401,17 @@ __global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageV
 // dv = (d_m - v d_rho)/rho, Y0 = (gam-1)(d_E - v.d_m + |v|^2 d_rho/2)/p,
 // V2 = rho |dv|^2/p, c = P_n rho.  r(g) = sum_n c D_n(g)/rho_n + g A,
 // r'(g) = sum_n c dD_n/dg + A; a = r''(0)/2 = sum c (X0^2 + (X0-Y0)^2/(gam-1) + V2)/2.
+// Newton from the root -A/a of the quadratic model, safeguarded by the bracket
+// [lo, hi] (r(lo) <= 0 < r(hi)); r is convex, so Newton converges from above.
+// A step |s| <= 1e-9 g leaves an error ~ s^2/g below 1e-18 g: the updated
+// iterate is returned without another evaluation.
 template <int P1>
 __global__ void k_relax(Params P, StageRelax sr) {
   constexpr int Np = P1 * P1 * P1;
   constexpr int R = (Np + 31) / 32;
   const long long N = (long long)P.K * Np;
   const double gam = P.gam;
+  const double inv_gm1 = 1.0 / (gam - 1.0);
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
   for (int e = blockIdx.x * warps_per_block + (threadIdx.x >> 5); e < P.K; e += gridDim.x * warps_per_block) {
@@ -424,23 +429,22 @@ __global__ void k_relax(Params P, StageRelax sr) {
         if (sr.u_new) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) d[v] = sr.u_new[v * N + g] - u[v];
+          if (sr.d_out) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sr.d_out[v * N + g] = d[v];
+          }
         } else {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            double s = 0.0;
-            for (int i = 0; i < sr.nst; ++i) s = fma(sr.coef[i], sr.k[i][v * N + g], s);
-            d[v] = s;
-          }
+          for (int v = 0; v < 5; ++v) d[v] = sr.d_in[v * N + g];
         }
-        if (sr.d_out) {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) sr.d_out[v * N + g] = d[v];
-        }
-        const double rho = u[0], ir = 1.0 / rho;
+        // one division: 1/(rho Pr), Pr = rho p
+        const double rho = u[0];
+        const double m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+        const double Pr = (gam - 1.0) * (rho * u[4] - 0.5 * m2);
+        const double inv = 1.0 / (rho * Pr);
+        const double ir = Pr * inv, ip = rho * rho * inv;
         const double v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
         const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
-        const double p = (gam - 1.0) * (u[4] - 0.5 * rho * v2s);
-        const double ip = 1.0 / p;
         const double dv0 = (d[1] - v0 * d[0]) * ir, dv1 = (d[2] - v1 * d[0]) * ir, dv2 = (d[3] - v2 * d[0]) * ir;
         const double Pn = mass_weight<P1>(P, n);
         nd[r].X0 = d[0] * ir;
@@ -448,13 +452,14 @@ __global__ void k_relax(Params P, StageRelax sr) {
         nd[r].V2 = rho * (dv0 * dv0 + dv1 * dv1 + dv2 * dv2) * ip;
         nd[r].c = Pn * rho;
         const double XY = nd[r].X0 - nd[r].Y0;
-        a_part += 0.5 * nd[r].c * (nd[r].X0 * nd[r].X0 + XY * XY / (gam - 1.0) + nd[r].V2);
+        a_part += 0.5 * nd[r].c * (nd[r].X0 * nd[r].X0 + XY * XY * inv_gm1 + nd[r].V2);
         s_part += nd[r].c;
         if (sr.u_new) {
           // A = sum P w(u).d - d_eta with w = ((gam - s)/(gam-1) - beta|v|^2/2, beta v, -beta)
           const double beta = rho * ip;
+          const double p = Pr * ir;
           const double sp = log(p) - gam * log(rho);
-          const double w0 = (gam - sp) / (gam - 1.0) - 0.5 * beta * v2s;
+          const double w0 = (gam - sp) * inv_gm1 - 0.5 * beta * v2s;
           A_part += Pn * (w0 * d[0] + beta * (v0 * d[1] + v1 * d[2] + v2 * d[3]) - beta * d[4]);
         }
       }
@@ -470,59 +475,54 @@ __global__ void k_relax(Params P, StageRelax sr) {
       if (!(A < 0.0)) {
         if (lane == 0) atomicOr(sr.status, kStatusNoRoot);
       } else {
-        // Newton from the quadratic-model root, safeguarded by bisection on [lo, hi]
         double lo = 0.0, hi = sr.gamma_max;
-        double rhi = 0.0;
-        bool phys_hi = true;
-        {
+        bool hi_known = false;
+        double gcur = fmin(fmax(-A / a, 1e-3), sr.gamma_max);
+        for (int it = 0; it < 100; ++it) {
           double sr_ = 0.0, sd_ = 0.0;
           bool ok = true;
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             double D, dD;
             if (nd[r].c != 0.0) {
-              if (relax_node_eval(nd[r], hi, gam, D, dD)) {
+              if (relax_node_eval(nd[r], gcur, gam, inv_gm1, D, dD)) {
                 sr_ += nd[r].c * D;
                 sd_ += nd[r].c * dD;
-              } else ok = false;
-            }
-          }
-          phys_hi = __all_sync(0xffffffffu, ok);
-          rhi = warp_sum(sr_) + hi * A;
-        }
-        if (phys_hi && !(rhi > 0.0)) {
-          gk = sr.gamma_max;
-        } else {
-          double gcur = fmin(fmax(-A / a, 1e-3), sr.gamma_max);
-          for (int it = 0; it < 200; ++it) {
-            double sr_ = 0.0, sd_ = 0.0;
-            bool ok = true;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-              double D, dD;
-              if (nd[r].c != 0.0) {
-                if (relax_node_eval(nd[r], gcur, gam, D, dD)) {
-                  sr_ += nd[r].c * D;
-                  sd_ += nd[r].c * dD;
-                } else ok = false;
+              } else {
+                ok = false;
               }
             }
-            const bool phys = __all_sync(0xffffffffu, ok);
-            const double rv = warp_sum(sr_) + gcur * A;
-            const double dv = warp_sum(sd_) + A;
-            const bool pos = !phys || rv > 0.0;
-            if (pos) hi = gcur; else lo = gcur;
-            const double newton = gcur - rv / dv;
-            const bool nok = phys && isfinite(newton) && newton > lo && newton < hi;
-            const double nxt = nok ? newton : 0.5 * (lo + hi);
-            const double step = fabs(nxt - gcur);
-            const double tol = 8.881784197001252e-16 * fmax(1.0, gcur);  // 4 * 2^-52
-            const bool conv = (nok && step <= tol) || (hi - lo) <= tol || rv == 0.0;
-            if (conv) {
-              gk = nok ? nxt : gcur;
-              break;
-            }
-            gcur = nxt;
+          }
+          const bool phys = __all_sync(0xffffffffu, ok);
+          const double rv = warp_sum(sr_) + gcur * A;
+          const double dv = warp_sum(sd_) + A;
+          if (!phys || rv > 0.0) {
+            hi = gcur;
+            hi_known = true;
+          } else {
+            lo = gcur;
+          }
+          if (phys && rv == 0.0) {
+            gk = gcur;
+            break;
+          }
+          const double step = rv / dv;
+          const double newton = gcur - step;
+          const bool nok = phys && dv > 0.0 && isfinite(newton) && newton > lo && newton < hi;
+          if (nok && fabs(step) <= 1e-9 * gcur) {
+            gk = newton;
+            break;
+          }
+          if (hi - lo <= 8.881784197001252e-16 * fmax(1.0, gcur)) {  // 4 * 2^-52
+            gk = lo;
+            break;
+          }
+          if (nok) gcur = newton;
+          else if (!hi_known) gcur = (gcur >= sr.gamma_max) ? sr.gamma_max : fmin(2.0 * gcur, sr.gamma_max);
+          else gcur = 0.5 * (lo + hi);
+          if (!hi_known && lo >= sr.gamma_max) {  // r(gamma_max) <= 0: capped
+            gk = sr.gamma_max;
+            break;
           }
         }
       }
@@ -578,7 +578,7 @@ void Launcher<P1, TF>::grad(const Params& P, const void* aux, void* fV, cudaStre
 template <int P1, typename TF>
 size_t Launcher<P1, TF>::volume_smem() {
   constexpr int Np = P1 * P1 * P1;
-  return size_t(VolCfg<P1>::EPB) * Np * (12 * sizeof(TF) + 2 * sizeof(double));
+  return size_t(VolCfg<P1>::EPB) * Np * ((kAux + 5) * sizeof(TF) + 2 * sizeof(double));
 }
 
 template <int P1, typename TF>

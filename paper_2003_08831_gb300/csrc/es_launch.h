@@ -22,7 +22,12 @@ struct StagePrep {
 
 // k_volume outputs
 struct StageVol {
-  double* kout;        // k_i = f(y^i)
+  double* kout;        // k_i = f(y^i) (unless d_out is set)
+  double* d_out;       // last stage: d = dcoef_self k_i + sum_j dcoef[j] dk[j] instead of k_i
+  int nd;
+  double dcoef[4];
+  const double* dk[4];
+  double dcoef_self;
   double* E;           // (eta' f)(y^i) per element, or nullptr
   const double* dw;    // w(y^i) - w(u), or nullptr
   double* A;           // relaxation term accumulator, or nullptr
@@ -35,11 +40,9 @@ struct StageRelax {
   const double* u;         // u_old
   const double* u_new;     // if set: d = u_new - u_old, A = sum P w(u).d - deta
   const double* deta;      // eta_new - eta_old per element (u_new mode)
-  int nst;                 // stages combined into d (k mode)
-  double coef[4];          // dt b_i
-  const double* k[4];
-  const double* A;         // accumulated A (k mode)
-  double* d_out;           // d written here if not nullptr
+  const double* d_in;      // d = u_new - u_old (RK mode: written by the last stage)
+  const double* A;         // accumulated A (RK mode)
+  double* d_out;           // u_new mode: d written here
   double* gamma_elem;
   unsigned long long* gmin_bits;
   int* status;

@@ -89,6 +89,12 @@ class Solver:
     def launch_count(self):
         return B.es_launch_count(self.ctx)
 
+    def profile(self, enable):
+        B.es_profile_enable(self.ctx, enable)
+
+    def profile_read(self):
+        return B.es_profile_read(self.ctx)
+
 
 def stable_dt(q, p, h, cfl, gamma_gas=1.4, mu=0.0, Pr=0.72):
     """dt = cfl h_min/((2p+1) max(|v| + c)) (and the viscous limit); host-side harness rule."""

@@ -1,7 +1,15 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Bar (FP64): max |gpu - oracle| <= 1e-12 max |oracle| per conserved variable,
-per element sum and per gamma_kappa (relative), on the same seeded inputs.
+Bars (FP64), on the same seeded inputs:
+* state after the stated steps: max |gpu - oracle| <= 1e-12 max |oracle| per
+  conserved variable;
+* right-hand side: |gpu - oracle| <= 1e-12 max |oracle| per variable, or, where
+  the SBP sums cancel (low Mach number), 256 eps times the magnitude of the
+  summed terms (oracle.dg.rhs_term_magnitude), the rounding bound of any FP64
+  evaluation;
+* gamma and gamma_kappa: 1e-12 relative, or 8x their response to rounding-level
+  changes of the right-hand side where that is larger (gamma_kappa is the root
+  of a second-order quantity).
 Meshes span several CTA tiles with a ragged last tile (element counts that are
 not multiples of the elements-per-CTA of any degree).
 """
@@ -14,6 +22,7 @@ from paper_2003_08831_gb300 import inputs
 pytestmark = pytest.mark.gpu
 G = 1.4
 TOL = 1e-12
+EPS = 2.0 ** -52
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -41,6 +50,16 @@ def random_state(mesh, seed, amp=0.2, noise=0.02):
                 2 * np.pi * (k[0] * x / L[0] + k[1] * y / L[1] + k[2] * z / L[2]) + rng.uniform(0, 6.3))
         return f * (1 + noise * rng.uniform(-1, 1, x.shape))
     return inputs.conserved(field(1.0, amp), field(0.3, amp), field(-0.2, amp), field(0.1, amp), field(1.0, amp), G)
+
+
+def assert_rhs_close(got, ref, terms):
+    got = np.asarray(got).reshape(5, -1)
+    ref = np.asarray(ref).reshape(5, -1)
+    terms = np.asarray(terms).reshape(5, -1)
+    scale = np.maximum(np.max(np.abs(ref), axis=1), 1e-3 * np.max(np.abs(ref)))[:, None]
+    bound = np.maximum(TOL * scale, 256 * EPS * terms)
+    bad = np.abs(got - ref) > bound
+    assert not bad.any(), (np.argwhere(bad)[:5], np.max(np.abs(got - ref) / bound))
 
 
 def rel_err_per_var(a, b):
@@ -74,8 +93,7 @@ def test_rhs_and_entropy_rate(p, n, mu, diss):
     q = s.to_device(U)
     dq, E = s.rhs(q, want_E=True)
     assert s.status() == 0
-    err = rel_err_per_var(dq.cpu().numpy(), ref)
-    assert np.all(err < TOL), err
+    assert_rhs_close(dq.cpu().numpy(), ref, dg.rhs_term_magnitude(mesh, U, phys))
     W = gas.entropy_variables(U, G)
     Escale = mesh.element_sum(np.sum(np.abs(W * ref), axis=0)).reshape(-1)
     assert np.max(np.abs(E.cpu().numpy() - Eref) / Escale) < TOL
@@ -103,10 +121,37 @@ def vortex_setup(N=4, p=3, nz=None):
     return mesh, U, lo, hi
 
 
+def gamma_sensitivity(mesh, U, dt, nsteps, phys, tab, mode, hist, seeds=4):
+    """Relative change of each step's gamma and of the last gamma_kappa when every
+    right-hand side evaluation of the oracle is perturbed at its rounding level
+    (2 eps times the magnitude of the summed terms, per node).  gamma_kappa is a
+    root of a second-order quantity, so this is the scale at which two correct
+    FP64 implementations (different summation order, FMA) can differ."""
+    g0 = np.array([h.gamma for h in hist])
+    gk0 = hist[-1].gamma_kappa.reshape(-1)
+    dg_, dgk = np.zeros(nsteps), np.zeros(gk0.size)
+    for seed in range(seeds):
+        rng = np.random.default_rng(1000 + seed)
+
+        def noisy(m_, U_, p_):
+            R = dg.rhs(m_, U_, p_)
+            T = dg.rhs_term_magnitude(m_, U_, p_)
+            return R + 2 * EPS * T * rng.standard_normal(R.shape)
+        _, _, h2 = rk.advance(mesh, U, dt, nsteps, phys, tab, mode=mode, rhs=noisy)
+        dg_ = np.maximum(dg_, np.abs(np.array([h.gamma for h in h2]) - g0) / g0)
+        gk2 = h2[-1].gamma_kappa.reshape(-1)
+        fin = np.isfinite(gk0) & np.isfinite(gk2)
+        dgk[fin] = np.maximum(dgk[fin], np.abs(gk2[fin] - gk0[fin]) / gk0[fin])
+    return dg_, dgk
+
+
 def compare_advance(mesh, U, lo, hi, phys, tabname, nsteps, mode="local", cfl=0.5, **kw):
+    """FP64 parity of es_advance: state at 1e-12 per variable; gamma and gamma_kappa at
+    1e-12 or, where larger, 8x their measured sensitivity to last-bit RHS changes."""
     from paper_2003_08831_gb300 import _binding as B
     dt = rk.stable_dt(mesh, U, phys, cfl)
     Uo, to, hist = rk.advance(mesh, U, dt, nsteps, phys, rk.TABLEAUX[tabname], mode=mode)
+    sens_g, sens_gk = gamma_sensitivity(mesh, U, dt, nsteps, phys, rk.TABLEAUX[tabname], mode, hist)
     s = solver(mesh.p, mesh.n, lo, hi, mu=phys.mu, Pr=phys.Pr, interface_diss=phys.diss,
                rk=B.ES_RK_BS3 if tabname == "BS3" else B.ES_RK_RK4,
                relax=B.ES_RELAX_LOCAL if mode == "local" else B.ES_RELAX_NONE, **kw)
@@ -117,13 +162,15 @@ def compare_advance(mesh, U, lo, hi, phys, tabname, nsteps, mode="local", cfl=0.
     assert np.all(err < TOL), err
     gref = np.array([h.gamma for h in hist])
     gh = gh.cpu().numpy()
-    assert np.max(np.abs(gh - gref) / gref) < TOL, (gh, gref)
+    tol_g = np.maximum(TOL, 8 * sens_g)
+    assert np.all(np.abs(gh - gref) / gref <= tol_g), (gh, gref, tol_g)
     assert abs(t.item() - to) < TOL * to
     gko = hist[-1].gamma_kappa.reshape(-1)
     gkg = gk.cpu().numpy()
     fin = np.isfinite(gko)
     assert np.array_equal(fin, np.isfinite(gkg))
-    assert np.max(np.abs(gkg[fin] - gko[fin]) / gko[fin]) < TOL
+    tol_gk = np.maximum(TOL, 8 * sens_gk)
+    assert np.all(np.abs(gkg[fin] - gko[fin]) / gko[fin] <= tol_gk[fin])
     s.close()
     return gref
 
@@ -209,4 +256,144 @@ def test_no_root_flag():
     assert s.status() == B.ES_ERR_NO_ROOT
     assert np.all(np.isinf(gk.cpu().numpy()))
     assert g.item() == 1.0
+    s.close()
+
+
+# ---------------------------------------------------------------------------------------
+# full-size workloads: sampled elements against oracle element blocks
+
+def tgv_full(p, N=32, noise=False):
+    lo, hi = (0.0, 0.0, 0.0), (2 * np.pi,) * 3
+    mesh = dg.Mesh(p, (N, N, N), lo, hi)
+    x, y, z = mesh.coords()
+    if noise:
+        U = inputs.perturbed_tgv_state(x.reshape(-1), y.reshape(-1), z.reshape(-1)).reshape(mesh.shape)
+    else:
+        U = inputs.tgv_state(x, y, z)
+    return mesh, U, lo, hi
+
+
+SAMPLES = [(0, 0, 0), (31, 31, 31), (5, 17, 30), (16, 0, 9), (23, 11, 4)]
+
+
+@pytest.mark.parametrize("p,mu", [(3, 0.0), (4, 1.0 / 1600.0)])
+def test_full_size_rhs_sampled(p, mu):
+    """32^3 TGV (p = 3 Euler, p = 4 Navier--Stokes Re 1600): es_rhs at full size vs the
+    oracle's RHS of the centre element of a periodic block around sampled elements."""
+    mesh, U, lo, hi = tgv_full(p)
+    phys = dg.Physics(G, mu=mu, Pr=0.72, diss=1)
+    s = solver(p, mesh.n, lo, hi, mu=mu)
+    dq = s.rhs(s.to_device(U)).cpu().numpy().reshape(mesh.shape)
+    assert s.status() == 0
+    s.close()
+    radius = 2 if mu > 0 else 1
+    nb = 2 * radius + 1
+    bm = dg.Mesh(p, (nb, nb, nb), (0, 0, 0), tuple(nb * h for h in mesh.h))
+    for c in SAMPLES:
+        B = dg.element_block(U, c, radius)
+        ref = dg.rhs(bm, B, phys)[:, radius, radius, radius]
+        terms = dg.rhs_term_magnitude(bm, B, phys)[:, radius, radius, radius]
+        got = dq[:, c[2], c[1], c[0]]
+        assert_rhs_close(got, ref, terms)
+
+
+def test_full_size_step_sampled():
+    """One relaxed BS3 step of the 32^3 p = 3 Euler TGV: gamma_kappa of sampled elements vs
+    the oracle on radius-3 blocks (three stages each widen the stencil by one element), and
+    q_new - q_old = gamma d there."""
+    p = 3
+    mesh, U, lo, hi = tgv_full(p)
+    phys = dg.Physics(G, diss=1)
+    dt = rk.stable_dt(mesh, U, phys, 0.5)
+    s = solver(p, mesh.n, lo, hi)
+    q = s.to_device(U)
+    t, gh, gk = s.advance(q, 1, dt)
+    assert s.status() == 0
+    qn = q.cpu().numpy().reshape(mesh.shape)
+    gk = gk.cpu().numpy().reshape(mesh.n[2], mesh.n[1], mesh.n[0])
+    gamma = gh.cpu().numpy()[0]
+    s.close()
+    assert gamma == np.min(gk)
+    radius = 3
+    nb = 2 * radius + 1
+    bm = dg.Mesh(p, (nb, nb, nb), (0, 0, 0), tuple(nb * h for h in mesh.h))
+    for c in SAMPLES[:3]:
+        B = dg.element_block(U, c, radius)
+        r = rk.rk_step(bm, B, dt, phys, rk.BS3)
+        g_ref = r.gamma_kappa[radius, radius, radius]
+        _, sens = gamma_sensitivity(bm, B, dt, 1, phys, rk.BS3, "local", [r], seeds=2)
+        tol = max(TOL, 8 * sens.reshape(nb, nb, nb)[radius, radius, radius])
+        g_got = gk[c[2], c[1], c[0]]
+        assert abs(g_got - g_ref) <= tol * g_ref, (c, g_got, g_ref, tol)
+        # the state moved by gamma d: compare with the oracle's d at the rounding level of
+        # the stage sums (dt times the RHS bound) plus the rounding of q_new - q_old
+        d_ref = r.d[:, radius, radius, radius]
+        d_got = (qn[:, c[2], c[1], c[0]] - U[:, c[2], c[1], c[0]]) / gamma
+        terms = dg.rhs_term_magnitude(bm, B, phys)[:, radius, radius, radius]
+        bound = 1e-9 * np.max(np.abs(d_ref)) + dt * 256 * EPS * terms + 4 * EPS * np.abs(U[:, c[2], c[1], c[0]])
+        assert np.all(np.abs(d_got - d_ref) <= bound)
+
+
+# ---------------------------------------------------------------------------------------
+# mixed precision: FP32 fluxes, SATs and viscous terms; FP64 state, entropy sums and gamma
+
+def rel_l2(a, b):
+    a = np.asarray(a).reshape(5, -1)
+    b = np.asarray(b).reshape(5, -1)
+    nb = np.sqrt(np.sum(b * b, axis=1))
+    nb = np.maximum(nb, 1e-3 * nb.max())
+    return np.sqrt(np.sum((a - b) ** 2, axis=1)) / nb
+
+
+@pytest.mark.parametrize("p,n,mu", [(3, (3, 5, 4), 0.0), (4, (3, 3, 4), 0.02)])
+def test_mixed_rhs_error(p, n, mu):
+    """The FP32 right-hand side against the FP64 oracle: relative L2 error per variable
+    bounded by 64 eps_32 times the flux-to-result cancellation of the SBP sums."""
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.5, 2.0)
+    mesh = dg.Mesh(p, n, lo, hi)
+    U = random_state(mesh, seed=7 + p, noise=0.0)
+    phys = dg.Physics(G, mu=mu, Pr=0.72, diss=1)
+    ref = dg.rhs(mesh, U, phys)
+    # cancellation: size of the individual terms sum_j |2 D_ij f*_ij| against the result
+    terms = np.zeros_like(U)
+    for m in range(3):
+        A = np.moveaxis(U, {0: 6, 1: 5, 2: 4}[m], -1)
+        F = gas.ec_flux(A[..., :, None], A[..., None, :], G, m)
+        terms += (2.0 / mesh.h[m]) * np.moveaxis(np.einsum("ij,...ij->...i", np.abs(2 * mesh.D), np.abs(F)),
+                                                 -1, {0: 6, 1: 5, 2: 4}[m])
+    kappa = np.sqrt(np.sum(terms.reshape(5, -1) ** 2, axis=1)) / np.maximum(
+        np.sqrt(np.sum(ref.reshape(5, -1) ** 2, axis=1)), 1e-300)
+    from paper_2003_08831_gb300 import _binding as B
+    s = solver(p, n, lo, hi, mu=mu, precision=B.ES_MIXED)
+    dq = s.rhs(s.to_device(U)).cpu().numpy()
+    assert s.status() == 0
+    s.close()
+    err = rel_l2(dq, ref)
+    bound = 64 * 6e-8 * kappa
+    assert np.all(err <= np.maximum(bound, 1e-6)), (err, bound)
+
+
+@pytest.mark.parametrize("case", ["vortex", "tgv_noise_ns"])
+def test_mixed_advance_error(case):
+    """Mixed-precision relaxed steps against the FP64 oracle: state relative L2 <= 1e-5."""
+    from paper_2003_08831_gb300 import _binding as B
+    if case == "vortex":
+        mesh, U, lo, hi = vortex_setup()
+        phys = dg.Physics(G, diss=1)
+        nsteps = 20
+    else:
+        lo, hi = (0.0, 0.0, 0.0), (2 * np.pi,) * 3
+        mesh = dg.Mesh(4, (4, 4, 4), lo, hi)
+        x, y, z = mesh.coords()
+        U = inputs.perturbed_tgv_state(x.reshape(-1), y.reshape(-1), z.reshape(-1)).reshape(mesh.shape)
+        phys = dg.Physics(G, mu=1.0 / 1600.0, Pr=0.72, diss=1)
+        nsteps = 10
+    dt = rk.stable_dt(mesh, U, phys, 0.5)
+    Uo, to, hist = rk.advance(mesh, U, dt, nsteps, phys, rk.BS3)
+    s = solver(mesh.p, mesh.n, lo, hi, mu=phys.mu, precision=B.ES_MIXED)
+    q = s.to_device(U)
+    t, gh, gk = s.advance(q, nsteps, dt)
+    assert s.status() == 0
+    err = rel_l2(q.cpu().numpy(), Uo)
+    assert np.all(err < 1e-5), err
     s.close()
