@@ -130,14 +130,16 @@ def advance(mesh, U, dt, nsteps, phys, tab, mode="local", t0=0.0, delta_floor=re
 
 
 def stable_dt(mesh, U, phys, cfl):
-    """dt = cfl * h_min / ((2p+1) lambda_max) (+ viscous limit); fixed for the run."""
+    """Fixed time step from the initial state (the paper states none; Section 4.1.1
+    only fixes U dt/dx).  Reading: the sum of the directional Courant numbers,
+    dt = cfl / ((2p+1) max_n sum_m (|v_m| + c)/h_m), and for mu > 0 also
+    dt <= cfl rho_min / (mu max(4/3, gamma/Pr) sum_m ((2p+1)/h_m)^2)."""
     g = phys.gamma
     rho, v, p = gas.primitives(U, g)
     c = np.sqrt(g * p / rho)
-    lam = np.max(np.sqrt(np.sum(v * v, axis=0)) + c)
-    hmin = float(np.min(mesh.h))
-    dt = cfl * hmin / ((2 * mesh.p + 1) * lam)
+    lam = np.max(sum((np.abs(v[m]) + c) / mesh.h[m] for m in range(3)))
+    dt = cfl / ((2 * mesh.p + 1) * lam)
     if phys.mu > 0.0:
-        hv = hmin / (2 * mesh.p + 1)
-        dt = min(dt, cfl * hv * hv * float(np.min(rho)) / (phys.mu * max(4.0 / 3.0, g / phys.Pr)))
+        k2 = sum(((2 * mesh.p + 1) / mesh.h[m]) ** 2 for m in range(3))
+        dt = min(dt, cfl * float(np.min(rho)) / (phys.mu * max(4.0 / 3.0, g / phys.Pr) * k2))
     return dt

@@ -97,15 +97,17 @@ class Solver:
 
 
 def stable_dt(q, p, h, cfl, gamma_gas=1.4, mu=0.0, Pr=0.72):
-    """dt = cfl h_min/((2p+1) max(|v| + c)) (and the viscous limit); host-side harness rule."""
+    """Host-side harness rule, fixed for the run: the sum of the directional
+    Courant numbers, dt = cfl / ((2p+1) max_n sum_m (|v_m| + c)/h_m), and for
+    mu > 0 also dt <= cfl rho_min / (mu max(4/3, gamma/Pr) sum_m ((2p+1)/h_m)^2)."""
     q = np.asarray(q).reshape(5, -1)
     rho = q[0]
     v = q[1:4] / rho
     pr = (gamma_gas - 1.0) * (q[4] - 0.5 * rho * np.sum(v * v, axis=0))
-    lam = np.max(np.sqrt(np.sum(v * v, axis=0)) + np.sqrt(gamma_gas * pr / rho))
-    hmin = float(np.min(h))
-    dt = cfl * hmin / ((2 * p + 1) * lam)
+    c = np.sqrt(gamma_gas * pr / rho)
+    lam = np.max(sum((np.abs(v[m]) + c) / h[m] for m in range(3)))
+    dt = cfl / ((2 * p + 1) * lam)
     if mu > 0.0:
-        hv = hmin / (2 * p + 1)
-        dt = min(dt, cfl * hv * hv * float(np.min(rho)) / (mu * max(4.0 / 3.0, gamma_gas / Pr)))
+        k2 = sum(((2 * p + 1) / h[m]) ** 2 for m in range(3))
+        dt = min(dt, cfl * float(np.min(rho)) / (mu * max(4.0 / 3.0, gamma_gas / Pr) * k2))
     return dt
