@@ -293,6 +293,8 @@ def main():
     ap.add_argument("--workload", default=MAIN, choices=sorted(WORKLOADS))
     ap.add_argument("--no-forms", action="store_true", help="skip the extra precision/physics forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed region only (no kernel-event pass, e2e, forms or CPU baseline): for profilers")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
@@ -324,6 +326,15 @@ def run_full(args, rank, world, local_rank):
     clocks = res.pop("clocks", None)
     nodes = res["nodes"]
     value = world * nodes * STAGES * args.steps / (ms / 1e3)
+    if args.quick:
+        res["solver"].close()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                              "quick": True, "config": {"workload": args.workload}}), flush=True)
+        if dist is not None:
+            dist.barrier()
+        return 0
     prof = kernel_profile(res, min(args.steps, 50))
     res["solver"].close()
     del res["q"], res["t"], res["solver"]
