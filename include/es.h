@@ -27,6 +27,8 @@
 #ifndef ES_H
 #define ES_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -37,6 +39,7 @@ extern "C" {
 #define ES_ERR_NONPHYSICAL (-3) /* rho <= 0 or p <= 0 met at some node */
 #define ES_ERR_NO_ROOT (-4)     /* an element had r'(0) >= 0: no positive gamma_kappa */
 #define ES_ERR_NOMEM (-6)       /* device or host allocation failed */
+#define ES_ERR_TOO_LARGE (-7)   /* problem exceeds the fixed scratch of es_rhs_noalloc */
 
 #define ES_RK_BS3 0 /* Bogacki--Shampine 3(2), b = (2/9, 1/3, 4/9, 0) */
 #define ES_RK_RK4 1 /* classical RK(4,4) */
@@ -133,6 +136,31 @@ long long es_launch_count(const es_ctx* ctx);
 #define ES_KERNEL_COUNT 6
 int es_profile_enable(es_ctx* ctx, int enable);
 int es_profile_read(es_ctx* ctx, double* ms, long long* launches);
+
+/* Right-hand side without a context: for callers that cannot call cudaMalloc
+ * (code running where the allocator is off limits, e.g. inside another
+ * library's allocation-free region or a host framework that owns all device
+ * memory).  The paper has no counterpart; it is the same operation as es_rhs
+ * (same kernels, same results) with the caller passing only inputs and
+ * outputs: q and dqdt (device, [5][K][Np]) and optionally E_elem (device, [K]).
+ *
+ * It allocates nothing: the kernels' scratch is one fixed array of
+ * ES_NOALLOC_SCRATCH_BYTES (32 MiB) of device memory compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Problems whose scratch (es_rhs_noalloc_scratch_bytes) exceeds it are
+ * rejected with ES_ERR_TOO_LARGE before any work is enqueued; invalid
+ * configurations return ES_ERR_INVALID.
+ *
+ * The first call on each device runs a one-time set-up (it looks up the
+ * array's device address with the device current and sets kernel attributes);
+ * make that first call before any stream capture.  All calls share the array
+ * and the status word inside it, so calls that overlap on the GPU (different
+ * streams, or different host threads) race: serialise them.  Device-side
+ * errors (non-physical states) are not reported by this call. */
+#define ES_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqdt, double* E_elem, void* stream);
+/* Scratch bytes es_rhs_noalloc needs for cfg (0 if cfg is invalid). */
+size_t es_rhs_noalloc_scratch_bytes(const es_config* cfg);
 
 /* Static message for an ES_* code. */
 const char* es_strerror(int code);

@@ -17,13 +17,14 @@ ES_ERR_CUDA = -2
 ES_ERR_NONPHYSICAL = -3
 ES_ERR_NO_ROOT = -4
 ES_ERR_NOMEM = -6
+ES_ERR_TOO_LARGE = -7
 ES_RK_BS3, ES_RK_RK4 = 0, 1
 ES_FP64, ES_MIXED = 0, 1
 ES_RELAX_NONE, ES_RELAX_LOCAL = 0, 1
 
 EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "es_advance",
            "es_advance_host", "es_node_coords", "es_status", "es_launch_count", "es_strerror",
-           "es_profile_enable", "es_profile_read"]
+           "es_profile_enable", "es_profile_read", "es_rhs_noalloc", "es_rhs_noalloc_scratch_bytes"]
 KERNEL_KINDS = ["prep", "face", "grad", "volume", "relax", "other"]
 
 
@@ -78,6 +79,10 @@ def load(path=None):
     lib.es_profile_enable.restype = i
     lib.es_profile_read.argtypes = [vp, vp, vp]
     lib.es_profile_read.restype = i
+    lib.es_rhs_noalloc.argtypes = [ctypes.POINTER(es_config), vp, vp, vp, vp]
+    lib.es_rhs_noalloc.restype = i
+    lib.es_rhs_noalloc_scratch_bytes.argtypes = [ctypes.POINTER(es_config)]
+    lib.es_rhs_noalloc_scratch_bytes.restype = ctypes.c_size_t
     lib.es_strerror.argtypes = [i]
     lib.es_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -195,3 +200,13 @@ def es_profile_read(ctx):
     n = np.zeros(len(KERNEL_KINDS), dtype=np.int64)
     _check(load().es_profile_read(ctx, _ptr(ms), _ptr(n)), "es_profile_read")
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def es_rhs_noalloc(cfg, q, dqdt, E_elem=None, stream=None):
+    """Right-hand side through the allocation-free entry point (no context)."""
+    _check(load().es_rhs_noalloc(ctypes.byref(cfg), _ptr(q), _ptr(dqdt), _ptr(E_elem), _stream(stream)),
+           "es_rhs_noalloc")
+
+
+def es_rhs_noalloc_scratch_bytes(cfg):
+    return int(load().es_rhs_noalloc_scratch_bytes(ctypes.byref(cfg)))

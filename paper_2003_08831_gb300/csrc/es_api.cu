@@ -64,7 +64,7 @@ void lgl_tables(int p, double* x, double* w, double* D) {
     x[p - i] = s;
   }
   if (p % 2 == 0) x[p / 2] = 0.0;
-  std::vector<double> Pv(n);
+  double Pv[kMaxP1];
   for (int i = 0; i < n; ++i) {
     double Pm;
     legendre_eval(p, x[i], &Pv[i], &Pm);
@@ -108,6 +108,69 @@ Tableau tableau(int rk) {
 
 }  // namespace
 
+
+namespace es {
+
+// Argument checks shared by every entry point that takes an es_config.
+int validate_config(const es_config& C) {
+  if (C.p < 2 || C.p > 5 || C.nx < 1 || C.ny < 1 || C.nz < 1) return ES_ERR_INVALID;
+  if (!(C.gamma_gas > 1.0) || !(C.R > 0.0) || C.mu < 0.0 || (C.mu > 0.0 && !(C.Pr > 0.0))) return ES_ERR_INVALID;
+  if (C.rk != ES_RK_BS3 && C.rk != ES_RK_RK4) return ES_ERR_INVALID;
+  if (C.precision != ES_FP64 && C.precision != ES_MIXED) return ES_ERR_INVALID;
+  if (C.relax != ES_RELAX_NONE && C.relax != ES_RELAX_LOCAL) return ES_ERR_INVALID;
+  if (C.interface_diss != 0 && C.interface_diss != 1) return ES_ERR_INVALID;
+  for (int m = 0; m < 3; ++m)
+    if (!(C.hi[m] > C.lo[m])) return ES_ERR_INVALID;
+  const long long K = (long long)C.nx * C.ny * C.nz;
+  if (K > (1LL << 30)) return ES_ERR_INVALID;
+  return ES_OK;
+}
+
+// Kernel parameters (LGL/SBP tables, metric, gas constants) of a configuration; host only,
+// no allocation.
+void build_params(const es_config& C, Params* out) {
+  Params& P = *out;
+  std::memset(&P, 0, sizeof(P));
+  const int P1 = C.p + 1;
+  double x[kMaxP1], w[kMaxP1], D[kMaxP1 * kMaxP1];
+  lgl_tables(C.p, x, w, D);
+  for (int i = 0; i < P1; ++i) {
+    P.omega[i] = w[i];
+    for (int j = 0; j < P1; ++j) {
+      P.D[i * P1 + j] = D[i * P1 + j];
+      P.D2[i * P1 + j] = (i == j) ? 0.0 : 2.0 * D[i * P1 + j];
+    }
+  }
+  P.inv_omega_end = 1.0 / w[0];
+  double h[3];
+  for (int m = 0; m < 3; ++m) {
+    const int nm = m == 0 ? C.nx : (m == 1 ? C.ny : C.nz);
+    h[m] = (C.hi[m] - C.lo[m]) / nm;
+    P.metric[m] = 2.0 / h[m];
+  }
+  P.J = h[0] * h[1] * h[2] / 8.0;
+  P.gam = C.gamma_gas;
+  P.mu = C.mu;
+  P.R = C.R;
+  P.kappa_heat = C.mu > 0.0 ? C.mu * C.gamma_gas * C.R / ((C.gamma_gas - 1.0) * C.Pr) : 0.0;
+  P.nx = C.nx;
+  P.ny = C.ny;
+  P.nz = C.nz;
+  P.K = C.nx * C.ny * C.nz;
+  P.diss = C.interface_diss;
+  P.p1 = P1;
+}
+
+int grid_for_sms(int sm_count, long long n, int block) {
+  long long g = (n + block - 1) / block;
+  const long long cap = (long long)sm_count * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace es
+
 // ---------------------------------------------------------------------------
 struct es_ctx {
   es_config cfg;
@@ -147,13 +210,7 @@ struct es_ctx {
 
 namespace {
 
-int grid_for(const es_ctx* c, long long n, int block) {
-  long long g = (n + block - 1) / block;
-  const long long cap = (long long)c->sm_count * 8;
-  if (g > cap) g = cap;
-  if (g < 1) g = 1;
-  return (int)g;
-}
+int grid_for(const es_ctx* c, long long n, int block) { return grid_for_sms(c->sm_count, n, block); }
 
 template <typename F>
 int dispatch(const es_ctx* c, F&& f) {
@@ -363,16 +420,8 @@ int es_create(const es_config* cfg, es_ctx** out) {
   *out = nullptr;
   if (!cfg) return ES_ERR_INVALID;
   const es_config& C = *cfg;
-  if (C.p < 2 || C.p > 5 || C.nx < 1 || C.ny < 1 || C.nz < 1) return ES_ERR_INVALID;
-  if (!(C.gamma_gas > 1.0) || !(C.R > 0.0) || C.mu < 0.0 || (C.mu > 0.0 && !(C.Pr > 0.0))) return ES_ERR_INVALID;
-  if (C.rk != ES_RK_BS3 && C.rk != ES_RK_RK4) return ES_ERR_INVALID;
-  if (C.precision != ES_FP64 && C.precision != ES_MIXED) return ES_ERR_INVALID;
-  if (C.relax != ES_RELAX_NONE && C.relax != ES_RELAX_LOCAL) return ES_ERR_INVALID;
-  if (C.interface_diss != 0 && C.interface_diss != 1) return ES_ERR_INVALID;
-  for (int m = 0; m < 3; ++m)
-    if (!(C.hi[m] > C.lo[m])) return ES_ERR_INVALID;
+  if (validate_config(C) != ES_OK) return ES_ERR_INVALID;
   const long long K = (long long)C.nx * C.ny * C.nz;
-  if (K > (1LL << 30)) return ES_ERR_INVALID;
 
   es_ctx* c = new (std::nothrow) es_ctx();
   if (!c) return ES_ERR_NOMEM;
@@ -390,35 +439,7 @@ int es_create(const es_config* cfg, es_ctx** out) {
     return ES_ERR_CUDA;
   }
 
-  Params& P = c->P;
-  std::memset(&P, 0, sizeof(P));
-  double x[kMaxP1], w[kMaxP1], D[kMaxP1 * kMaxP1];
-  lgl_tables(C.p, x, w, D);
-  for (int i = 0; i < c->P1; ++i) {
-    P.omega[i] = w[i];
-    for (int j = 0; j < c->P1; ++j) {
-      P.D[i * c->P1 + j] = D[i * c->P1 + j];
-      P.D2[i * c->P1 + j] = (i == j) ? 0.0 : 2.0 * D[i * c->P1 + j];
-    }
-  }
-  P.inv_omega_end = 1.0 / w[0];
-  double h[3];
-  for (int m = 0; m < 3; ++m) {
-    const int nm = m == 0 ? C.nx : (m == 1 ? C.ny : C.nz);
-    h[m] = (C.hi[m] - C.lo[m]) / nm;
-    P.metric[m] = 2.0 / h[m];
-  }
-  P.J = h[0] * h[1] * h[2] / 8.0;
-  P.gam = C.gamma_gas;
-  P.mu = C.mu;
-  P.R = C.R;
-  P.kappa_heat = C.mu > 0.0 ? C.mu * C.gamma_gas * C.R / ((C.gamma_gas - 1.0) * C.Pr) : 0.0;
-  P.nx = C.nx;
-  P.ny = C.ny;
-  P.nz = C.nz;
-  P.K = c->K;
-  P.diss = C.interface_diss;
-  P.p1 = c->P1;
+  build_params(C, &c->P);
 
   const long long N = c->N;
   const long long P2 = (long long)c->P1 * c->P1;
@@ -601,6 +622,7 @@ const char* es_strerror(int code) {
     case ES_ERR_NONPHYSICAL: return "non-physical state (rho <= 0 or p <= 0)";
     case ES_ERR_NO_ROOT: return "no positive relaxation root (r'(0) >= 0)";
     case ES_ERR_NOMEM: return "out of memory";
+    case ES_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of es_rhs_noalloc";
   }
   return "unknown error";
 }

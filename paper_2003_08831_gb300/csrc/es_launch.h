@@ -3,9 +3,15 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "../../include/es.h"
 #include "es_device.cuh"
 
 namespace es {
+
+// host helpers shared by the entry points (es_api.cu)
+int validate_config(const es_config& C);
+void build_params(const es_config& C, Params* out);
+int grid_for_sms(int sm_count, long long n, int block);
 
 // k_prep: stage state y = u (+ gamma d first) + sum_j coef[j] k[j]
 struct StagePrep {
