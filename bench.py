@@ -385,10 +385,14 @@ def run_full(args, rank, world, local_rank):
             w2 = WORKLOADS[name]
             steps2 = 50
             r2 = measure_device(w2, steps2, 3)
+            p2 = kernel_profile(r2, 20)
             r2["solver"].close()
+            t2 = sum(v[0] for v in p2.values())
             forms[name] = {"value": r2["nodes"] * STAGES * steps2 / (r2["ms"] / 1e3),
                            "ms_per_step": r2["ms"] / steps2, "steps": steps2,
-                           "gamma_range": [r2["gamma_min"], r2["gamma_max"]], "launches": int(r2["launches"])}
+                           "gamma_range": [r2["gamma_min"], r2["gamma_max"]], "launches": int(r2["launches"]),
+                           "kernel_share": {k: round(v[0] / t2, 4) for k, v in p2.items() if v[1] > 0},
+                           "speedup_vs_fp64_same_physics": None}
             del r2
         out["forms"] = forms
     print(json.dumps(out), flush=True)

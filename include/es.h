@@ -162,6 +162,45 @@ int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqdt, double* 
 /* Scratch bytes es_rhs_noalloc needs for cfg (0 if cfg is invalid). */
 size_t es_rhs_noalloc_scratch_bytes(const es_config* cfg);
 
+/* Volume-kernel tile autotuning for this context: times every tile variant
+ * (elements per CTA x threads) of the flux-differencing kernel on the state q
+ * (device, [5][K][Np]) and keeps the fastest for later calls.  Synchronises. */
+int es_autotune(es_ctx* ctx, const double* q, void* stream);
+
+/* ---- Batches: many independent instances advanced together -------------
+ * Instances may differ in LGL degree and element counts (and box) but share
+ * the physics and method fields of es_config (gamma_gas, mu, Pr, R,
+ * interface_diss, relax, rk, precision, delta_floor); otherwise
+ * ES_ERR_INVALID.  Instances of one degree form one group stored as one SoA
+ * over the group's elements; each step of all groups is captured once in a
+ * CUDA graph (one kernel per phase and degree, groups on parallel branches)
+ * and replayed.  Every instance has its own dt, gamma (= min over its own
+ * elements, Theorem 2.3) and t.  The batch owns the states (device memory). */
+typedef struct es_batch es_batch;
+int es_batch_create(const es_config* cfgs, int count, es_batch** out);
+void es_batch_destroy(es_batch* b);
+/* nodes of instance inst, or of the whole batch for inst = -1; -1 on error */
+long long es_batch_nodes(const es_batch* b, int inst);
+/* node coordinates xyz[3][K_i][Np_i] of instance inst (host) */
+int es_batch_node_coords(const es_batch* b, int inst, double* xyz_host);
+/* copy instance inst's state [5][K_i][Np_i] in from / out to host memory (synchronous) */
+int es_batch_set_state(es_batch* b, int inst, const double* q_host);
+int es_batch_get_state(es_batch* b, int inst, double* q_host);
+/* per-instance time steps dt_host[count] (> 0); required before es_batch_advance */
+int es_batch_set_dt(es_batch* b, const double* dt_host);
+/* tile autotuning per degree group on the current states (invalidates the graph) */
+int es_batch_autotune(es_batch* b, void* stream);
+/* the volume tile variant chosen for instance inst's group */
+int es_batch_volume_variant(const es_batch* b, int inst);
+/* nsteps relaxed steps of every instance (graph replay), ordered after prior
+ * work on `stream`; later work on `stream` waits for it */
+int es_batch_advance(es_batch* b, int nsteps, void* stream);
+/* per-instance t and last gamma (host arrays of count, either may be NULL); synchronises */
+int es_batch_times(es_batch* b, double* t_host, double* gamma_host);
+int es_batch_status(es_batch* b, void* stream);
+/* kernels enqueued (graph replays count every kernel of the step) */
+long long es_batch_launch_count(const es_batch* b);
+
 /* Static message for an ES_* code. */
 const char* es_strerror(int code);
 

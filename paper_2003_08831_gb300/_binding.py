@@ -24,7 +24,11 @@ ES_RELAX_NONE, ES_RELAX_LOCAL = 0, 1
 
 EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "es_advance",
            "es_advance_host", "es_node_coords", "es_status", "es_launch_count", "es_strerror",
-           "es_profile_enable", "es_profile_read", "es_rhs_noalloc", "es_rhs_noalloc_scratch_bytes"]
+           "es_profile_enable", "es_profile_read", "es_rhs_noalloc", "es_rhs_noalloc_scratch_bytes",
+           "es_autotune", "es_batch_create", "es_batch_destroy", "es_batch_nodes", "es_batch_node_coords",
+           "es_batch_set_state", "es_batch_get_state", "es_batch_set_dt", "es_batch_autotune",
+           "es_batch_volume_variant", "es_batch_advance", "es_batch_times", "es_batch_status",
+           "es_batch_launch_count"]
 KERNEL_KINDS = ["prep", "face", "grad", "volume", "relax", "other"]
 
 
@@ -83,6 +87,34 @@ def load(path=None):
     lib.es_rhs_noalloc.restype = i
     lib.es_rhs_noalloc_scratch_bytes.argtypes = [ctypes.POINTER(es_config)]
     lib.es_rhs_noalloc_scratch_bytes.restype = ctypes.c_size_t
+    lib.es_autotune.argtypes = [vp, vp, vp]
+    lib.es_autotune.restype = i
+    lib.es_batch_create.argtypes = [ctypes.POINTER(es_config), i, ctypes.POINTER(vp)]
+    lib.es_batch_create.restype = i
+    lib.es_batch_destroy.argtypes = [vp]
+    lib.es_batch_destroy.restype = None
+    lib.es_batch_nodes.argtypes = [vp, i]
+    lib.es_batch_nodes.restype = ctypes.c_longlong
+    lib.es_batch_node_coords.argtypes = [vp, i, vp]
+    lib.es_batch_node_coords.restype = i
+    lib.es_batch_set_state.argtypes = [vp, i, vp]
+    lib.es_batch_set_state.restype = i
+    lib.es_batch_get_state.argtypes = [vp, i, vp]
+    lib.es_batch_get_state.restype = i
+    lib.es_batch_set_dt.argtypes = [vp, vp]
+    lib.es_batch_set_dt.restype = i
+    lib.es_batch_autotune.argtypes = [vp, vp]
+    lib.es_batch_autotune.restype = i
+    lib.es_batch_volume_variant.argtypes = [vp, i]
+    lib.es_batch_volume_variant.restype = i
+    lib.es_batch_advance.argtypes = [vp, i, vp]
+    lib.es_batch_advance.restype = i
+    lib.es_batch_times.argtypes = [vp, vp, vp]
+    lib.es_batch_times.restype = i
+    lib.es_batch_status.argtypes = [vp, vp]
+    lib.es_batch_status.restype = i
+    lib.es_batch_launch_count.argtypes = [vp]
+    lib.es_batch_launch_count.restype = ctypes.c_longlong
     lib.es_strerror.argtypes = [i]
     lib.es_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -210,3 +242,64 @@ def es_rhs_noalloc(cfg, q, dqdt, E_elem=None, stream=None):
 
 def es_rhs_noalloc_scratch_bytes(cfg):
     return int(load().es_rhs_noalloc_scratch_bytes(ctypes.byref(cfg)))
+
+
+def es_autotune(ctx, q, stream=None):
+    _check(load().es_autotune(ctx, _ptr(q), _stream(stream)), "es_autotune")
+
+
+# ---- batches ---------------------------------------------------------------------------------
+
+def es_batch_create(cfgs):
+    arr = (es_config * len(cfgs))(*cfgs)
+    b = ctypes.c_void_p()
+    _check(load().es_batch_create(arr, len(cfgs), ctypes.byref(b)), "es_batch_create")
+    return b
+
+
+def es_batch_destroy(b):
+    load().es_batch_destroy(b)
+
+
+def es_batch_nodes(b, inst=-1):
+    return int(load().es_batch_nodes(b, int(inst)))
+
+
+def es_batch_node_coords(b, inst, xyz_host):
+    _check(load().es_batch_node_coords(b, int(inst), _ptr(xyz_host)), "es_batch_node_coords")
+
+
+def es_batch_set_state(b, inst, q_host):
+    _check(load().es_batch_set_state(b, int(inst), _ptr(q_host)), "es_batch_set_state")
+
+
+def es_batch_get_state(b, inst, q_host):
+    _check(load().es_batch_get_state(b, int(inst), _ptr(q_host)), "es_batch_get_state")
+
+
+def es_batch_set_dt(b, dt_host):
+    _check(load().es_batch_set_dt(b, _ptr(dt_host)), "es_batch_set_dt")
+
+
+def es_batch_autotune(b, stream=None):
+    _check(load().es_batch_autotune(b, _stream(stream)), "es_batch_autotune")
+
+
+def es_batch_volume_variant(b, inst):
+    return int(load().es_batch_volume_variant(b, int(inst)))
+
+
+def es_batch_advance(b, nsteps, stream=None):
+    _check(load().es_batch_advance(b, int(nsteps), _stream(stream)), "es_batch_advance")
+
+
+def es_batch_times(b, t_host=None, gamma_host=None):
+    _check(load().es_batch_times(b, _ptr(t_host), _ptr(gamma_host)), "es_batch_times")
+
+
+def es_batch_status(b, stream=None):
+    return load().es_batch_status(b, _stream(stream))
+
+
+def es_batch_launch_count(b):
+    return int(load().es_batch_launch_count(b))

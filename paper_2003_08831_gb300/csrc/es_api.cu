@@ -126,6 +126,24 @@ int validate_config(const es_config& C) {
   return ES_OK;
 }
 
+// Geometry of the instance described by C, its first element at off.
+InstGeom instance_geom(const es_config& C, int off) {
+  InstGeom g;
+  g.nx = C.nx;
+  g.ny = C.ny;
+  g.nz = C.nz;
+  g.off = off;
+  double h[3];
+  for (int m = 0; m < 3; ++m) {
+    const int nm = m == 0 ? C.nx : (m == 1 ? C.ny : C.nz);
+    h[m] = (C.hi[m] - C.lo[m]) / nm;
+    g.metric[m] = 2.0 / h[m];
+  }
+  g.J = h[0] * h[1] * h[2] / 8.0;
+  g.dt = 0.0;
+  return g;
+}
+
 // Kernel parameters (LGL/SBP tables, metric, gas constants) of a configuration; host only,
 // no allocation.
 void build_params(const es_config& C, Params* out) {
@@ -142,23 +160,17 @@ void build_params(const es_config& C, Params* out) {
     }
   }
   P.inv_omega_end = 1.0 / w[0];
-  double h[3];
-  for (int m = 0; m < 3; ++m) {
-    const int nm = m == 0 ? C.nx : (m == 1 ? C.ny : C.nz);
-    h[m] = (C.hi[m] - C.lo[m]) / nm;
-    P.metric[m] = 2.0 / h[m];
-  }
-  P.J = h[0] * h[1] * h[2] / 8.0;
   P.gam = C.gamma_gas;
   P.mu = C.mu;
   P.R = C.R;
   P.kappa_heat = C.mu > 0.0 ? C.mu * C.gamma_gas * C.R / ((C.gamma_gas - 1.0) * C.Pr) : 0.0;
-  P.nx = C.nx;
-  P.ny = C.ny;
-  P.nz = C.nz;
   P.K = C.nx * C.ny * C.nz;
   P.diss = C.interface_diss;
   P.p1 = P1;
+  P.ninst = 1;
+  P.g0 = instance_geom(C, 0);
+  P.geom = nullptr;
+  P.elem_inst = nullptr;
 }
 
 int grid_for_sms(int sm_count, long long n, int block) {
@@ -172,16 +184,18 @@ int grid_for_sms(int sm_count, long long n, int block) {
 }  // namespace es
 
 // ---------------------------------------------------------------------------
-struct es_ctx {
-  es_config cfg;
-  int P1, Np, K;
-  long long N;  // K * Np
+// A group: instances sharing the LGL degree and the physics, stored as one SoA
+// over the group's elements.  The single-instance context is a group of one;
+// a batch is one group per degree.
+struct Group {
+  es_config cfg;  // physics (and, for a context, the mesh)
+  int P1 = 0, Np = 0, K = 0, ninst = 0;
+  long long N = 0;
+  size_t tf = 8;  // bytes per flux value (8 FP64, 4 mixed)
   Params P;
-  Tableau tab;
-  int sm_count;
-  int device;
-  size_t tf;  // bytes per flux value (8 FP64, 4 mixed)
-  // workspace
+  int vol_variant = 0;
+  std::vector<InstGeom> geom;      // host copy of the instance table
+  std::vector<int> inst_ids;       // batch instance index of each local instance
   double* k[4] = {nullptr, nullptr, nullptr, nullptr};
   void* aux = nullptr;
   void* F = nullptr;
@@ -190,16 +204,23 @@ struct es_ctx {
   double* d = nullptr;
   double* A = nullptr;
   double* gamma_elem = nullptr;
-  double* scal = nullptr;  // [0] gamma_cur, [1] t scratch
-  unsigned long long* gmin = nullptr;
+  double* gamma_cur = nullptr;           // [ninst]
+  unsigned long long* gmin = nullptr;    // [ninst]
+  int* pending = nullptr;                // [ninst]
+  double* t = nullptr;                   // [ninst] (batch)
+  double* q = nullptr;                   // group-owned state (batch)
+  InstGeom* geom_dev = nullptr;
+  int* elem_inst_dev = nullptr;
+};
+
+// Launch bookkeeping shared by a context or a batch.
+struct Engine {
+  int device = 0, sm_count = 0;
   int* status = nullptr;
-  // host-buffer path
-  double* q_host_dev = nullptr;
-  double* t_host_dev = nullptr;
-  double* hist_host_dev = nullptr;
-  int hist_cap = 0;
+  Tableau tab;
+  int relax = 1;
   long long launches = 0;
-  // per-kernel event timing (es_profile_enable)
+  bool capturing = false;
   bool profiling = false;
   struct Mark { int kind; cudaEvent_t a, b; };
   std::vector<Mark> marks;
@@ -208,20 +229,28 @@ struct es_ctx {
   long long prof_n[ES_KERNEL_COUNT] = {0};
 };
 
+struct es_ctx {
+  Engine eng;
+  Group g;
+  double* q_host_dev = nullptr;
+  double* t_host_dev = nullptr;
+  double* hist_host_dev = nullptr;
+  int hist_cap = 0;
+};
+
+struct es_batch {
+  Engine eng;
+  std::vector<Group> groups;
+  std::vector<std::pair<int, int>> where;  // instance -> (group, local instance)
+  std::vector<es_config> cfgs;
+  std::vector<cudaStream_t> side;          // one stream per group for graph capture
+  std::vector<cudaEvent_t> fork, join;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t exec_stream = nullptr;
+  long long kernels_per_step = 0;
+};
+
 namespace {
-
-int grid_for(const es_ctx* c, long long n, int block) { return grid_for_sms(c->sm_count, n, block); }
-
-template <typename F>
-int dispatch(const es_ctx* c, F&& f) {
-  switch (c->P1) {
-    case 3: return c->tf == 8 ? f(Launcher<3, double>()) : f(Launcher<3, float>());
-    case 4: return c->tf == 8 ? f(Launcher<4, double>()) : f(Launcher<4, float>());
-    case 5: return c->tf == 8 ? f(Launcher<5, double>()) : f(Launcher<5, float>());
-    case 6: return c->tf == 8 ? f(Launcher<6, double>()) : f(Launcher<6, float>());
-  }
-  return ES_ERR_INVALID;
-}
 
 int cuda_check(cudaError_t e) {
   if (e != cudaSuccess) {
@@ -241,172 +270,362 @@ int dev_alloc(T** p, size_t count) {
   return ES_OK;
 }
 
-void free_ctx(es_ctx* c) {
-  if (!c) return;
-  for (auto& m : c->marks) {
+int dev_alloc_bytes(void** p, size_t bytes) {
+  if (bytes == 0) { *p = nullptr; return ES_OK; }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) { *p = nullptr; cudaGetLastError(); return ES_ERR_NOMEM; }
+  return ES_OK;
+}
+
+template <typename F>
+int dispatch(const Group& g, F&& f) {
+  switch (g.P1) {
+    case 3: return g.tf == 8 ? f(Launcher<3, double>()) : f(Launcher<3, float>());
+    case 4: return g.tf == 8 ? f(Launcher<4, double>()) : f(Launcher<4, float>());
+    case 5: return g.tf == 8 ? f(Launcher<5, double>()) : f(Launcher<5, float>());
+    case 6: return g.tf == 8 ? f(Launcher<6, double>()) : f(Launcher<6, float>());
+  }
+  return ES_ERR_INVALID;
+}
+
+int engine_init(Engine& e, const es_config& C) {
+  if (cudaGetDevice(&e.device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&e.sm_count, cudaDevAttrMultiProcessorCount, e.device) != cudaSuccess) {
+    cudaGetLastError();
+    return ES_ERR_CUDA;
+  }
+  e.tab = tableau(C.rk);
+  e.relax = C.relax;
+  int rc = dev_alloc(&e.status, 1);
+  if (rc == ES_OK) rc = cuda_check(cudaMemset(e.status, 0, sizeof(int)));
+  return rc;
+}
+
+void engine_free(Engine& e) {
+  for (auto& m : e.marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
   }
-  for (auto e : c->pool) cudaEventDestroy(e);
-  for (auto& p : c->k) cudaFree(p);
-  cudaFree(c->aux);
-  cudaFree(c->F);
-  cudaFree(c->fV);
-  cudaFree(c->dw);
-  cudaFree(c->d);
-  cudaFree(c->A);
-  cudaFree(c->gamma_elem);
-  cudaFree(c->scal);
-  cudaFree(c->gmin);
-  cudaFree(c->status);
-  cudaFree(c->q_host_dev);
-  cudaFree(c->t_host_dev);
-  cudaFree(c->hist_host_dev);
-  delete c;
+  for (auto ev : e.pool) cudaEventDestroy(ev);
+  e.marks.clear();
+  e.pool.clear();
+  cudaFree(e.status);
+  e.status = nullptr;
 }
 
-cudaEvent_t take_event(es_ctx* c) {
-  if (!c->pool.empty()) {
-    cudaEvent_t e = c->pool.back();
-    c->pool.pop_back();
-    return e;
+cudaEvent_t take_event(Engine& e) {
+  if (!e.pool.empty()) {
+    cudaEvent_t ev = e.pool.back();
+    e.pool.pop_back();
+    return ev;
   }
-  cudaEvent_t e = nullptr;
-  cudaEventCreate(&e);
-  return e;
+  cudaEvent_t ev = nullptr;
+  cudaEventCreate(&ev);
+  return ev;
 }
 
 // Folds recorded event pairs into the per-kind totals (synchronises the device).
-void flush_marks(es_ctx* c) {
-  if (c->marks.empty()) return;
+void flush_marks(Engine& e) {
+  if (e.marks.empty()) return;
   cudaDeviceSynchronize();
-  for (auto& m : c->marks) {
+  for (auto& m : e.marks) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
-      c->prof_ms[m.kind] += ms;
-      c->prof_n[m.kind] += 1;
+      e.prof_ms[m.kind] += ms;
+      e.prof_n[m.kind] += 1;
     }
-    c->pool.push_back(m.a);
-    c->pool.push_back(m.b);
+    e.pool.push_back(m.a);
+    e.pool.push_back(m.b);
   }
-  c->marks.clear();
+  e.marks.clear();
   cudaGetLastError();
 }
 
-// Brackets one launch with events when profiling is on.
+// Brackets one launch with events when profiling is on (not while capturing a graph).
 template <typename Fn>
-void timed(es_ctx* c, int kind, cudaStream_t st, Fn&& fn) {
-  c->launches += 1;
-  if (!c->profiling) {
+void timed(Engine& e, int kind, cudaStream_t st, Fn&& fn) {
+  e.launches += 1;
+  if (!e.profiling || e.capturing) {
     fn();
     return;
   }
-  if (c->marks.size() >= 4096) flush_marks(c);
-  es_ctx::Mark m{kind, take_event(c), take_event(c)};
+  if (e.marks.size() >= 4096) flush_marks(e);
+  Engine::Mark m{kind, take_event(e), take_event(e)};
   cudaEventRecord(m.a, st);
   fn();
   cudaEventRecord(m.b, st);
-  c->marks.push_back(m);
+  e.marks.push_back(m);
 }
 
-// One stage's right-hand side into kout (+ element sums), on state
-// u (+ update) + sum_j coef[j] k[j].
-int run_stage(es_ctx* c, const StagePrep& sp, const StageVol& sv, cudaStream_t st) {
-  const bool ns = c->cfg.mu != 0.0;
-  return dispatch(c, [&](auto L) {
+void group_free(Group& g) {
+  for (auto& p : g.k) cudaFree(p);
+  cudaFree(g.aux);
+  cudaFree(g.F);
+  cudaFree(g.fV);
+  cudaFree(g.dw);
+  cudaFree(g.d);
+  cudaFree(g.A);
+  cudaFree(g.gamma_elem);
+  cudaFree(g.gamma_cur);
+  cudaFree(g.gmin);
+  cudaFree(g.pending);
+  cudaFree(g.t);
+  cudaFree(g.q);
+  cudaFree(g.geom_dev);
+  cudaFree(g.elem_inst_dev);
+  g = Group();
+}
+
+// Allocates a group for the instances `insts` (same degree and physics).
+int group_init(Group& g, const es_config* insts, int n, int stages, bool own_state) {
+  const es_config& C = insts[0];
+  g.cfg = C;
+  g.P1 = C.p + 1;
+  g.Np = g.P1 * g.P1 * g.P1;
+  g.ninst = n;
+  g.tf = C.precision == ES_MIXED ? 4 : 8;
+  build_params(C, &g.P);
+  long long K = 0;
+  g.geom.resize(n);
+  for (int i = 0; i < n; ++i) {
+    g.geom[i] = instance_geom(insts[i], (int)K);
+    K += (long long)insts[i].nx * insts[i].ny * insts[i].nz;
+  }
+  if (K > (1LL << 30)) return ES_ERR_INVALID;
+  g.K = (int)K;
+  g.N = K * g.Np;
+  g.P.K = g.K;
+  g.P.ninst = n;
+  g.P.g0 = g.geom[0];
+  const long long N = g.N;
+  const long long P2 = (long long)g.P1 * g.P1;
+  int rc = ES_OK;
+  for (int i = 0; i < stages && rc == ES_OK; ++i) rc = dev_alloc(&g.k[i], 5 * N);
+  if (rc == ES_OK) rc = dev_alloc_bytes(&g.aux, kAuxPlanes * N * g.tf);
+  if (rc == ES_OK) rc = dev_alloc_bytes(&g.F, 15 * K * P2 * g.tf);
+  if (rc == ES_OK && C.mu > 0.0) rc = dev_alloc_bytes(&g.fV, 12 * N * g.tf);
+  if (rc == ES_OK) rc = dev_alloc(&g.dw, 5 * N);
+  if (rc == ES_OK) rc = dev_alloc(&g.d, 5 * N);
+  if (rc == ES_OK) rc = dev_alloc(&g.A, K);
+  if (rc == ES_OK) rc = dev_alloc(&g.gamma_elem, K);
+  if (rc == ES_OK) rc = dev_alloc(&g.gamma_cur, n);
+  if (rc == ES_OK) rc = dev_alloc(&g.gmin, n);
+  if (rc == ES_OK) rc = dev_alloc(&g.pending, n);
+  if (rc == ES_OK) rc = dev_alloc(&g.t, n);
+  if (rc == ES_OK && own_state) rc = dev_alloc(&g.q, 5 * N);
+  if (rc == ES_OK) rc = cuda_check(cudaMemset(g.pending, 0, n * sizeof(int)));
+  if (rc == ES_OK) rc = cuda_check(cudaMemset(g.gamma_cur, 0, n * sizeof(double)));
+  if (rc == ES_OK) rc = cuda_check(cudaMemset(g.t, 0, n * sizeof(double)));
+  if (rc == ES_OK && own_state) rc = cuda_check(cudaMemset(g.q, 0, 5 * N * sizeof(double)));
+  if (rc == ES_OK && own_state) {  // batches: device instance tables (dt can change without re-capture)
+    std::vector<int> ei(K);
+    for (int i = 0; i < n; ++i) {
+      const long long Ki = (long long)insts[i].nx * insts[i].ny * insts[i].nz;
+      for (long long e = 0; e < Ki; ++e) ei[g.geom[i].off + e] = i;
+    }
+    rc = dev_alloc(&g.geom_dev, n);
+    if (rc == ES_OK) rc = dev_alloc(&g.elem_inst_dev, K);
+    if (rc == ES_OK) rc = cuda_check(cudaMemcpy(g.geom_dev, g.geom.data(), n * sizeof(InstGeom), cudaMemcpyHostToDevice));
+    if (rc == ES_OK) rc = cuda_check(cudaMemcpy(g.elem_inst_dev, ei.data(), K * sizeof(int), cudaMemcpyHostToDevice));
+    g.P.geom = g.geom_dev;
+    g.P.elem_inst = g.elem_inst_dev;
+  }
+  if (rc == ES_OK) rc = dispatch(g, [&](auto L) { return cuda_check(decltype(L)::volume_setup()); });
+  return rc;
+}
+
+int grid_for(const Engine& e, long long n, int block) { return grid_for_sms(e.sm_count, n, block); }
+
+// One stage's right-hand side into kout or d (+ element sums), on state u (+ pending
+// update) + dt sum_j coef[j] k[j].
+int run_stage(Engine& E, Group& g, const StagePrep& sp, const StageVol& sv, cudaStream_t st) {
+  const bool ns = g.cfg.mu != 0.0;
+  return dispatch(g, [&](auto L) {
     using Lc = decltype(L);
-    timed(c, ES_KERNEL_PREP, st, [&] { Lc::prep(c->P, sp, c->aux, c->status, st, grid_for(c, c->N, 256)); });
-    timed(c, ES_KERNEL_FACE, st,
-          [&] { Lc::face(c->P, c->aux, c->F, st, grid_for(c, 3LL * c->K * c->P1 * c->P1, 256)); });
-    if (ns) timed(c, ES_KERNEL_GRAD, st, [&] { Lc::grad(c->P, c->aux, c->fV, st, grid_for(c, c->N, 256)); });
-    timed(c, ES_KERNEL_VOLUME, st, [&] { Lc::volume(c->P, sv, c->aux, c->F, c->fV, ns, st); });
+    timed(E, ES_KERNEL_PREP, st, [&] { Lc::prep(g.P, sp, g.aux, E.status, st, grid_for(E, g.N, 256)); });
+    timed(E, ES_KERNEL_FACE, st,
+          [&] { Lc::face(g.P, g.aux, g.F, st, grid_for(E, 3LL * g.K * g.P1 * g.P1, 256)); });
+    if (ns) timed(E, ES_KERNEL_GRAD, st, [&] { Lc::grad(g.P, g.aux, g.fV, st, grid_for(E, g.N, 256)); });
+    timed(E, ES_KERNEL_VOLUME, st, [&] { Lc::volume(g.P, sv, g.aux, g.F, g.fV, ns, st, g.vol_variant); });
     return last_launch_error();
   });
 }
 
-int run_relax(es_ctx* c, const StageRelax& sr, cudaStream_t st) {
-  const int grid = (int)std::min<long long>((c->K + 3) / 4, (long long)c->sm_count * 16);
-  return dispatch(c, [&](auto L) {
-    timed(c, ES_KERNEL_RELAX, st, [&] { decltype(L)::relax(c->P, sr, st, grid); });
+int run_relax(Engine& E, Group& g, const StageRelax& sr, cudaStream_t st) {
+  const int grid = (int)std::min<long long>((g.K + 3) / 4, (long long)E.sm_count * 16);
+  return dispatch(g, [&](auto L) {
+    timed(E, ES_KERNEL_RELAX, st, [&] { decltype(L)::relax(g.P, sr, st, grid); });
     return last_launch_error();
   });
 }
 
-StageRelax relax_base(es_ctx* c) {
+StageRelax relax_base(Engine& E, Group& g) {
   StageRelax sr;
   std::memset(&sr, 0, sizeof(sr));
-  sr.gamma_elem = c->gamma_elem;
-  sr.gmin_bits = c->gmin;
-  sr.status = c->status;
-  sr.delta_floor = c->cfg.delta_floor > 0.0 ? c->cfg.delta_floor : 1e-8;
+  sr.gamma_elem = g.gamma_elem;
+  sr.gmin_bits = g.gmin;
+  sr.status = E.status;
+  sr.delta_floor = g.cfg.delta_floor > 0.0 ? g.cfg.delta_floor : 1e-8;
   sr.gamma_max = 8.0;
   return sr;
 }
 
-// nsteps relaxed steps on device state q (in place).
+// One relaxed step of every instance of the group on state q: all stages, the
+// gamma_kappa solve, gamma = min, t += gamma dt, pending update flag set.  The
+// update u += gamma d itself runs in the next step's first k_prep (or group_finish).
+// hist (device, per instance) receives gamma if not null.
+int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStream_t st) {
+  const Tableau& T = E.tab;
+  const bool relax = E.relax == ES_RELAX_LOCAL;
+  int rc = ES_OK;
+  for (int i = 0; i < T.s && rc == ES_OK; ++i) {
+    StagePrep sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.q = q;
+    sp.d = g.d;
+    sp.gamma_cur = g.gamma_cur;
+    sp.pending = (i == 0) ? g.pending : nullptr;
+    sp.Np = g.Np;
+    for (int j = 0; j < i; ++j) {
+      if (T.a[i][j] != 0.0) {
+        sp.coef[sp.nprev] = T.a[i][j];
+        sp.k[sp.nprev] = g.k[j];
+        sp.nprev++;
+      }
+    }
+    const bool want_dw = relax && i > 0 && T.b[i] != 0.0;
+    sp.dw = want_dw ? g.dw : nullptr;
+    StageVol sv;
+    std::memset(&sv, 0, sizeof(sv));
+    sv.kout = g.k[i];
+    if (i == T.s - 1) {  // last stage: write d = dt sum_j b_j k_j instead of k_s
+      sv.d_out = g.d;
+      sv.dcoef_self = T.b[i];
+      for (int j = 0; j < i; ++j) {
+        if (T.b[j] != 0.0) {
+          sv.dcoef[sv.nd] = T.b[j];
+          sv.dk[sv.nd] = g.k[j];
+          sv.nd++;
+        }
+      }
+    }
+    sv.dw = want_dw ? g.dw : nullptr;
+    sv.A = relax ? g.A : nullptr;
+    sv.A_scale = -T.b[i];
+    sv.A_init = (i == 0);
+    rc = run_stage(E, g, sp, sv, st);
+  }
+  if (rc != ES_OK) return rc;
+  StageRelax sr = relax_base(E, g);
+  sr.u = q;
+  sr.d_in = g.d;
+  sr.A = g.A;
+  if (!relax) sr.delta_floor = INFINITY;  // every element unconstrained: gamma = 1
+  rc = run_relax(E, g, sr, st);
+  if (rc != ES_OK) return rc;
+  timed(E, ES_KERNEL_OTHER, st, [&] { launch_scalar(g.P, g.gmin, g.gamma_cur, t, hist, g.pending, relax ? 1 : 0, st); });
+  return last_launch_error();
+}
+
+// Applies the pending relaxed update of every instance and clears the flags.
+int group_finish(Engine& E, Group& g, double* q, cudaStream_t st) {
+  timed(E, ES_KERNEL_OTHER, st,
+        [&] { launch_update(g.P, q, q, g.d, g.gamma_cur, g.pending, g.Np, st, grid_for(E, 5 * g.N, 256)); });
+  timed(E, ES_KERNEL_OTHER, st, [&] { launch_reset(g.gmin, g.pending, g.ninst, st); });
+  return last_launch_error();
+}
+
+// nsteps relaxed steps of a single-instance context on device state q (in place).
 int advance_device(es_ctx* c, double* q, int nsteps, double dt, double* t, double* hist, double* gamma_elem_out,
                    cudaStream_t st) {
-  const Tableau& T = c->tab;
-  const bool relax = c->cfg.relax == ES_RELAX_LOCAL;
+  Group& g = c->g;
+  g.P.g0.dt = dt;
   int rc = ES_OK;
-  timed(c, ES_KERNEL_OTHER, st, [&] { launch_reset_min(c->gmin, st); });
+  timed(c->eng, ES_KERNEL_OTHER, st, [&] { launch_reset(g.gmin, g.pending, g.ninst, st); });
   for (int n = 0; n < nsteps && rc == ES_OK; ++n) {
-    for (int i = 0; i < T.s && rc == ES_OK; ++i) {
-      StagePrep sp;
-      std::memset(&sp, 0, sizeof(sp));
-      sp.q = q;
-      sp.d = c->d;
-      sp.gamma_cur = c->scal;
-      sp.apply_update = (i == 0 && n > 0);
-      sp.Np = c->Np;
-      for (int j = 0; j < i; ++j) {
-        if (T.a[i][j] != 0.0) {
-          sp.coef[sp.nprev] = dt * T.a[i][j];
-          sp.k[sp.nprev] = c->k[j];
-          sp.nprev++;
-        }
-      }
-      const bool want_dw = relax && i > 0 && T.b[i] != 0.0;
-      sp.dw = want_dw ? c->dw : nullptr;
-      StageVol sv;
-      std::memset(&sv, 0, sizeof(sv));
-      sv.kout = c->k[i];
-      if (i == T.s - 1) {  // last stage: write d = dt sum_j b_j k_j instead of k_s
-        sv.d_out = c->d;
-        sv.dcoef_self = dt * T.b[i];
-        for (int j = 0; j < i; ++j) {
-          if (T.b[j] != 0.0) {
-            sv.dcoef[sv.nd] = dt * T.b[j];
-            sv.dk[sv.nd] = c->k[j];
-            sv.nd++;
-          }
-        }
-      }
-      sv.dw = want_dw ? c->dw : nullptr;
-      sv.A = relax ? c->A : nullptr;
-      sv.A_scale = -dt * T.b[i];
-      sv.A_init = (i == 0);
-      rc = run_stage(c, sp, sv, st);
-    }
-    if (rc != ES_OK) break;
-    StageRelax sr = relax_base(c);
-    sr.u = q;
-    sr.d_in = c->d;
-    sr.A = c->A;
-    if (!relax) sr.delta_floor = INFINITY;  // combine only: every element unconstrained
-    rc = run_relax(c, sr, st);
-    if (rc != ES_OK) break;
-    timed(c, ES_KERNEL_OTHER, st,
-          [&] { launch_scalar(c->gmin, c->scal, t ? t : c->scal + 1, hist, n, dt, relax ? 1 : 0, st); });
-    if (gamma_elem_out && n == nsteps - 1)
-      rc = cuda_check(cudaMemcpyAsync(gamma_elem_out, c->gamma_elem, sizeof(double) * c->K,
+    rc = group_step(c->eng, g, q, t ? t : g.t, hist ? hist + n : nullptr, st);
+    if (rc == ES_OK && gamma_elem_out && n == nsteps - 1)
+      rc = cuda_check(cudaMemcpyAsync(gamma_elem_out, g.gamma_elem, sizeof(double) * g.K,
                                       cudaMemcpyDeviceToDevice, st));
   }
-  if (rc == ES_OK && nsteps > 0) {
-    timed(c, ES_KERNEL_OTHER, st,
-          [&] { launch_update(q, q, c->d, c->scal, 5 * c->N, st, grid_for(c, 5 * c->N, 256)); });
-    rc = last_launch_error();
+  if (rc == ES_OK && nsteps > 0) rc = group_finish(c->eng, g, q, st);
+  return rc;
+}
+
+// Node coordinates [3][K][Np] of the mesh of C (host).
+void node_coords(const es_config& C, double* xyz) {
+  double x[kMaxP1], w[kMaxP1], D[kMaxP1 * kMaxP1];
+  lgl_tables(C.p, x, w, D);
+  const int P1 = C.p + 1;
+  const int Np = P1 * P1 * P1;
+  const int K = C.nx * C.ny * C.nz;
+  const long long N = (long long)K * Np;
+  const int nxyz[3] = {C.nx, C.ny, C.nz};
+  for (int e = 0; e < K; ++e) {
+    const int ei[3] = {e % nxyz[0], (e / nxyz[0]) % nxyz[1], e / (nxyz[0] * nxyz[1])};
+    for (int n = 0; n < Np; ++n) {
+      const int ni[3] = {n % P1, (n / P1) % P1, n / (P1 * P1)};
+      for (int m = 0; m < 3; ++m) {
+        const double h = (C.hi[m] - C.lo[m]) / nxyz[m];
+        xyz[m * N + (long long)e * Np + n] = C.lo[m] + h * (ei[m] + 0.5 * (1.0 + x[ni[m]]));
+      }
+    }
   }
+}
+
+int status_read(Engine& E, cudaStream_t st) {
+  int h = 0;
+  int rc = cuda_check(cudaMemcpyAsync(&h, E.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (rc == ES_OK) rc = cuda_check(cudaStreamSynchronize(st));
+  if (rc != ES_OK) return rc;
+  if (h) {
+    rc = cuda_check(cudaMemsetAsync(E.status, 0, sizeof(int), st));
+    if (rc == ES_OK) rc = cuda_check(cudaStreamSynchronize(st));
+    if (rc != ES_OK) return rc;
+  }
+  if (h & kStatusNonphysical) return ES_ERR_NONPHYSICAL;
+  if (h & kStatusNoRoot) return ES_ERR_NO_ROOT;
+  return ES_OK;
+}
+
+// Times each volume tile on the group's current state (one stage's RHS) and keeps the fastest.
+int autotune_group(Engine& E, Group& g, const double* q, cudaStream_t st) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return ES_ERR_CUDA;
+  float best = 1e30f;
+  int best_v = 0;
+  const int keep = g.vol_variant;
+  const bool prof = E.profiling;
+  E.profiling = false;
+  int rc = ES_OK;
+  for (int v = 0; v < kVolumeVariants && rc == ES_OK; ++v) {
+    g.vol_variant = v;
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3 && rc == ES_OK; ++rep) {
+      StagePrep sp;
+      std::memset(&sp, 0, sizeof(sp));
+      sp.q = const_cast<double*>(q);
+      sp.Np = g.Np;
+      StageVol sv;
+      std::memset(&sv, 0, sizeof(sv));
+      sv.kout = g.k[0];
+      cudaEventRecord(a, st);
+      rc = run_stage(E, g, sp, sv, st);
+      cudaEventRecord(b, st);
+      if (rc == ES_OK) rc = cuda_check(cudaEventSynchronize(b));
+      float ms = 0.f;
+      if (rc == ES_OK) rc = cuda_check(cudaEventElapsedTime(&ms, a, b));
+      if (ms < tmin) tmin = ms;
+    }
+    if (rc == ES_OK && tmin < best) {
+      best = tmin;
+      best_v = v;
+    }
+  }
+  E.profiling = prof;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  g.vol_variant = rc == ES_OK ? best_v : keep;
   return rc;
 }
 
@@ -421,55 +640,29 @@ int es_create(const es_config* cfg, es_ctx** out) {
   if (!cfg) return ES_ERR_INVALID;
   const es_config& C = *cfg;
   if (validate_config(C) != ES_OK) return ES_ERR_INVALID;
-  const long long K = (long long)C.nx * C.ny * C.nz;
-
   es_ctx* c = new (std::nothrow) es_ctx();
   if (!c) return ES_ERR_NOMEM;
-  c->cfg = C;
-  c->P1 = C.p + 1;
-  c->Np = c->P1 * c->P1 * c->P1;
-  c->K = (int)K;
-  c->N = K * c->Np;
-  c->tf = C.precision == ES_MIXED ? 4 : 8;
-  c->tab = tableau(C.rk);
-  if (cudaGetDevice(&c->device) != cudaSuccess ||
-      cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
-    cudaGetLastError();
-    delete c;
-    return ES_ERR_CUDA;
-  }
-
-  build_params(C, &c->P);
-
-  const long long N = c->N;
-  const long long P2 = (long long)c->P1 * c->P1;
-  int rc = ES_OK;
-  for (int i = 0; i < c->tab.s && rc == ES_OK; ++i) rc = dev_alloc(&c->k[i], 5 * N);
-  if (rc == ES_OK) rc = cuda_check(cudaMalloc(&c->aux, kAux * N * c->tf)) == ES_OK ? ES_OK : ES_ERR_NOMEM;
-  if (rc == ES_OK) rc = cuda_check(cudaMalloc(&c->F, 15 * K * P2 * c->tf)) == ES_OK ? ES_OK : ES_ERR_NOMEM;
-  if (rc == ES_OK && C.mu > 0.0) rc = cuda_check(cudaMalloc(&c->fV, 12 * N * c->tf)) == ES_OK ? ES_OK : ES_ERR_NOMEM;
-  if (rc == ES_OK) rc = dev_alloc(&c->dw, 5 * N);
-  if (rc == ES_OK) rc = dev_alloc(&c->d, 5 * N);
-  if (rc == ES_OK) rc = dev_alloc(&c->A, K);
-  if (rc == ES_OK) rc = dev_alloc(&c->gamma_elem, K);
-  if (rc == ES_OK) rc = dev_alloc(&c->scal, 2);
-  if (rc == ES_OK) rc = dev_alloc(&c->gmin, 1);
-  if (rc == ES_OK) rc = dev_alloc(&c->status, 1);
-  if (rc == ES_OK) rc = cuda_check(cudaMemset(c->status, 0, sizeof(int)));
-  if (rc == ES_OK) rc = cuda_check(cudaMemset(c->scal, 0, 2 * sizeof(double)));
-  if (rc == ES_OK) rc = dispatch(c, [&](auto L) { return cuda_check(decltype(L)::volume_setup()); });
+  int rc = engine_init(c->eng, C);
+  if (rc == ES_OK) rc = group_init(c->g, &C, 1, c->eng.tab.s, false);
   if (rc != ES_OK) {
-    free_ctx(c);
+    group_free(c->g);
+    engine_free(c->eng);
+    delete c;
     return rc;
   }
   *out = c;
   return ES_OK;
 }
 
-void es_destroy(es_ctx* ctx) {
-  if (!ctx) return;
+void es_destroy(es_ctx* c) {
+  if (!c) return;
   cudaDeviceSynchronize();
-  free_ctx(ctx);
+  group_free(c->g);
+  engine_free(c->eng);
+  cudaFree(c->q_host_dev);
+  cudaFree(c->t_host_dev);
+  cudaFree(c->hist_host_dev);
+  delete c;
 }
 
 int es_rhs(es_ctx* c, const double* q, double* dqdt, double* E_elem, void* stream) {
@@ -477,21 +670,22 @@ int es_rhs(es_ctx* c, const double* q, double* dqdt, double* E_elem, void* strea
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   StagePrep sp;
   std::memset(&sp, 0, sizeof(sp));
-  sp.q = const_cast<double*>(q);  // read only: apply_update = 0
-  sp.Np = c->Np;
+  sp.q = const_cast<double*>(q);  // read only: no pending update
+  sp.Np = c->g.Np;
   StageVol sv;
   std::memset(&sv, 0, sizeof(sv));
   sv.kout = dqdt;
   sv.E = E_elem;
-  return run_stage(c, sp, sv, st);
+  return run_stage(c->eng, c->g, sp, sv, st);
 }
 
 int es_entropy(es_ctx* c, const double* q, double* eta, void* stream) {
   if (!c || !q || !eta) return ES_ERR_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int grid = (int)std::min<long long>((c->K + 3) / 4, (long long)c->sm_count * 16);
-  return dispatch(c, [&](auto L) {
-    timed(c, ES_KERNEL_OTHER, st, [&] { decltype(L)::entropy(c->P, q, eta, st, grid); });
+  Group& g = c->g;
+  const int grid = (int)std::min<long long>((g.K + 3) / 4, (long long)c->eng.sm_count * 16);
+  return dispatch(g, [&](auto L) {
+    timed(c->eng, ES_KERNEL_OTHER, st, [&] { decltype(L)::entropy(g.P, q, eta, st, grid); });
     return last_launch_error();
   });
 }
@@ -500,24 +694,33 @@ int es_relax_step(es_ctx* c, const double* u_old, const double* u_new, const dou
                   double* gamma, double* u_out, void* stream) {
   if (!c || !u_old || !u_new || !d_eta || !u_out || u_out == u_old) return ES_ERR_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  timed(c, ES_KERNEL_OTHER, st, [&] { launch_reset_min(c->gmin, st); });
-  StageRelax sr = relax_base(c);
+  Engine& E = c->eng;
+  Group& g = c->g;
+  Params P = g.P;
+  P.g0.dt = 0.0;
+  timed(E, ES_KERNEL_OTHER, st, [&] { launch_reset(g.gmin, g.pending, g.ninst, st); });
+  StageRelax sr = relax_base(E, g);
   sr.u = u_old;
   sr.u_new = u_new;
   sr.deta = d_eta;
-  sr.d_out = c->d;
-  int rc = run_relax(c, sr, st);
+  sr.d_out = g.d;
+  int rc = dispatch(g, [&](auto L) {
+    const int grid = (int)std::min<long long>((g.K + 3) / 4, (long long)E.sm_count * 16);
+    timed(E, ES_KERNEL_RELAX, st, [&] { decltype(L)::relax(P, sr, st, grid); });
+    return last_launch_error();
+  });
   if (rc != ES_OK) return rc;
-  timed(c, ES_KERNEL_OTHER, st, [&] { launch_scalar(c->gmin, c->scal, c->scal + 1, nullptr, 0, 0.0, 1, st); });
-  timed(c, ES_KERNEL_OTHER, st,
-        [&] { launch_update(u_out, u_old, c->d, c->scal, 5 * c->N, st, grid_for(c, 5 * c->N, 256)); });
+  timed(E, ES_KERNEL_OTHER, st, [&] { launch_scalar(P, g.gmin, g.gamma_cur, g.t, nullptr, g.pending, 1, st); });
+  timed(E, ES_KERNEL_OTHER, st,
+        [&] { launch_update(P, u_out, u_old, g.d, g.gamma_cur, g.pending, g.Np, st, grid_for(E, 5 * g.N, 256)); });
+  timed(E, ES_KERNEL_OTHER, st, [&] { launch_reset(g.gmin, g.pending, g.ninst, st); });
   rc = last_launch_error();
   if (rc != ES_OK) return rc;
   if (gamma_elem) {
-    rc = cuda_check(cudaMemcpyAsync(gamma_elem, c->gamma_elem, sizeof(double) * c->K, cudaMemcpyDeviceToDevice, st));
+    rc = cuda_check(cudaMemcpyAsync(gamma_elem, g.gamma_elem, sizeof(double) * g.K, cudaMemcpyDeviceToDevice, st));
     if (rc != ES_OK) return rc;
   }
-  if (gamma) rc = cuda_check(cudaMemcpyAsync(gamma, c->scal, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (gamma) rc = cuda_check(cudaMemcpyAsync(gamma, g.gamma_cur, sizeof(double), cudaMemcpyDeviceToDevice, st));
   return rc;
 }
 
@@ -532,7 +735,7 @@ int es_advance_host(es_ctx* c, double* q_host, int nsteps, double dt, double* t_
   if (!c || !q_host || !t_host || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return ES_ERR_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = ES_OK;
-  if (!c->q_host_dev) rc = dev_alloc(&c->q_host_dev, 5 * c->N);
+  if (!c->q_host_dev) rc = dev_alloc(&c->q_host_dev, 5 * c->g.N);
   if (rc == ES_OK && !c->t_host_dev) rc = dev_alloc(&c->t_host_dev, 1);
   if (rc == ES_OK && gamma_hist_host && c->hist_cap < nsteps) {
     cudaFree(c->hist_host_dev);
@@ -542,7 +745,7 @@ int es_advance_host(es_ctx* c, double* q_host, int nsteps, double dt, double* t_
     if (rc == ES_OK) c->hist_cap = nsteps;
   }
   if (rc != ES_OK) return rc;
-  const size_t qb = sizeof(double) * 5 * c->N;
+  const size_t qb = sizeof(double) * 5 * c->g.N;
   rc = cuda_check(cudaMemcpyAsync(c->q_host_dev, q_host, qb, cudaMemcpyHostToDevice, st));
   if (rc == ES_OK) rc = cuda_check(cudaMemcpyAsync(c->t_host_dev, t_host, sizeof(double), cudaMemcpyHostToDevice, st));
   if (rc == ES_OK)
@@ -556,60 +759,39 @@ int es_advance_host(es_ctx* c, double* q_host, int nsteps, double dt, double* t_
   return rc;
 }
 
+int es_autotune(es_ctx* c, const double* q, void* stream) {
+  if (!c || !q) return ES_ERR_INVALID;
+  return autotune_group(c->eng, c->g, q, static_cast<cudaStream_t>(stream));
+}
+
 int es_node_coords(const es_ctx* c, double* xyz) {
   if (!c || !xyz) return ES_ERR_INVALID;
-  double x[kMaxP1], w[kMaxP1], D[kMaxP1 * kMaxP1];
-  lgl_tables(c->cfg.p, x, w, D);
-  const int P1 = c->P1;
-  const long long N = c->N;
-  const int nxyz[3] = {c->cfg.nx, c->cfg.ny, c->cfg.nz};
-  for (int e = 0; e < c->K; ++e) {
-    const int ei[3] = {e % nxyz[0], (e / nxyz[0]) % nxyz[1], e / (nxyz[0] * nxyz[1])};
-    for (int n = 0; n < c->Np; ++n) {
-      const int ni[3] = {n % P1, (n / P1) % P1, n / (P1 * P1)};
-      for (int m = 0; m < 3; ++m) {
-        const double h = (c->cfg.hi[m] - c->cfg.lo[m]) / nxyz[m];
-        xyz[m * N + (long long)e * c->Np + n] = c->cfg.lo[m] + h * (ei[m] + 0.5 * (1.0 + x[ni[m]]));
-      }
-    }
-  }
+  node_coords(c->g.cfg, xyz);
   return ES_OK;
 }
 
 int es_status(es_ctx* c, void* stream) {
   if (!c) return ES_ERR_INVALID;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int h = 0;
-  int rc = cuda_check(cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  if (rc == ES_OK) rc = cuda_check(cudaStreamSynchronize(st));
-  if (rc != ES_OK) return rc;
-  if (h) {
-    rc = cuda_check(cudaMemsetAsync(c->status, 0, sizeof(int), st));
-    if (rc == ES_OK) rc = cuda_check(cudaStreamSynchronize(st));
-    if (rc != ES_OK) return rc;
-  }
-  if (h & kStatusNonphysical) return ES_ERR_NONPHYSICAL;
-  if (h & kStatusNoRoot) return ES_ERR_NO_ROOT;
-  return ES_OK;
+  return status_read(c->eng, static_cast<cudaStream_t>(stream));
 }
 
-long long es_launch_count(const es_ctx* c) { return c ? c->launches : 0; }
+long long es_launch_count(const es_ctx* c) { return c ? c->eng.launches : 0; }
 
 int es_profile_enable(es_ctx* c, int enable) {
   if (!c) return ES_ERR_INVALID;
-  if (!enable) flush_marks(c);
-  c->profiling = enable != 0;
+  if (!enable) flush_marks(c->eng);
+  c->eng.profiling = enable != 0;
   return ES_OK;
 }
 
 int es_profile_read(es_ctx* c, double* ms, long long* launches) {
   if (!c || !ms || !launches) return ES_ERR_INVALID;
-  flush_marks(c);
+  flush_marks(c->eng);
   for (int k = 0; k < ES_KERNEL_COUNT; ++k) {
-    ms[k] = c->prof_ms[k];
-    launches[k] = c->prof_n[k];
-    c->prof_ms[k] = 0.0;
-    c->prof_n[k] = 0;
+    ms[k] = c->eng.prof_ms[k];
+    launches[k] = c->eng.prof_n[k];
+    c->eng.prof_ms[k] = 0.0;
+    c->eng.prof_n[k] = 0;
   }
   return ES_OK;
 }
@@ -629,40 +811,286 @@ const char* es_strerror(int code) {
 
 }  // extern "C"
 
+
+// ---------------------------------------------------------------------------
+// Batches: independent instances grouped by degree, one captured graph per step.
+namespace {
+
+bool same_physics(const es_config& a, const es_config& b) {
+  return a.gamma_gas == b.gamma_gas && a.mu == b.mu && (a.mu == 0.0 || a.Pr == b.Pr) && a.R == b.R &&
+         a.interface_diss == b.interface_diss && a.relax == b.relax && a.rk == b.rk && a.precision == b.precision &&
+         a.delta_floor == b.delta_floor;
+}
+
+void batch_free(es_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto s : b->side) cudaStreamDestroy(s);
+  for (auto e : b->fork) cudaEventDestroy(e);
+  for (auto e : b->join) cudaEventDestroy(e);
+  if (b->exec_stream) cudaStreamDestroy(b->exec_stream);
+  for (auto& g : b->groups) group_free(g);
+  engine_free(b->eng);
+  delete b;
+}
+
+int batch_capture(es_batch* b) {
+  Engine& E = b->eng;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  const long long before = E.launches;
+  E.capturing = true;
+  int rc = cuda_check(cudaStreamBeginCapture(b->exec_stream, cudaStreamCaptureModeThreadLocal));
+  for (size_t gi = 0; gi < b->groups.size() && rc == ES_OK; ++gi) {
+    Group& g = b->groups[gi];
+    rc = cuda_check(cudaEventRecord(b->fork[gi], b->exec_stream));
+    if (rc == ES_OK) rc = cuda_check(cudaStreamWaitEvent(b->side[gi], b->fork[gi], 0));
+    if (rc == ES_OK) rc = group_step(E, g, g.q, g.t, nullptr, b->side[gi]);
+    if (rc == ES_OK) rc = cuda_check(cudaEventRecord(b->join[gi], b->side[gi]));
+    if (rc == ES_OK) rc = cuda_check(cudaStreamWaitEvent(b->exec_stream, b->join[gi], 0));
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(b->exec_stream, &graph);
+  E.capturing = false;
+  if (rc == ES_OK) rc = cuda_check(ec);
+  if (rc == ES_OK) rc = cuda_check(cudaGraphInstantiate(&b->exec, graph, 0));
+  if (graph) cudaGraphDestroy(graph);
+  b->kernels_per_step = E.launches - before;
+  E.launches = before;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int es_batch_create(const es_config* cfgs, int count, es_batch** out) {
+  if (!out) return ES_ERR_INVALID;
+  *out = nullptr;
+  if (!cfgs || count < 1) return ES_ERR_INVALID;
+  for (int i = 0; i < count; ++i)
+    if (validate_config(cfgs[i]) != ES_OK || !same_physics(cfgs[0], cfgs[i])) return ES_ERR_INVALID;
+  es_batch* b = new (std::nothrow) es_batch();
+  if (!b) return ES_ERR_NOMEM;
+  b->cfgs.assign(cfgs, cfgs + count);
+  b->where.resize(count);
+  int rc = engine_init(b->eng, cfgs[0]);
+  for (int p = 2; p <= 5 && rc == ES_OK; ++p) {
+    std::vector<es_config> insts;
+    std::vector<int> ids;
+    for (int i = 0; i < count; ++i)
+      if (cfgs[i].p == p) {
+        insts.push_back(cfgs[i]);
+        ids.push_back(i);
+      }
+    if (insts.empty()) continue;
+    b->groups.emplace_back();
+    Group& g = b->groups.back();
+    rc = group_init(g, insts.data(), (int)insts.size(), b->eng.tab.s, true);
+    g.inst_ids = ids;
+    for (size_t j = 0; j < ids.size(); ++j) b->where[ids[j]] = {(int)b->groups.size() - 1, (int)j};
+  }
+  if (rc == ES_OK) rc = cuda_check(cudaStreamCreateWithFlags(&b->exec_stream, cudaStreamNonBlocking));
+  for (size_t gi = 0; gi < b->groups.size() && rc == ES_OK; ++gi) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t f = nullptr, j = nullptr;
+    rc = cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    if (rc == ES_OK) rc = cuda_check(cudaEventCreateWithFlags(&f, cudaEventDisableTiming));
+    if (rc == ES_OK) rc = cuda_check(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
+    b->side.push_back(s);
+    b->fork.push_back(f);
+    b->join.push_back(j);
+  }
+  if (rc != ES_OK) {
+    batch_free(b);
+    return rc;
+  }
+  *out = b;
+  return ES_OK;
+}
+
+void es_batch_destroy(es_batch* b) { batch_free(b); }
+
+long long es_batch_nodes(const es_batch* b, int inst) {
+  if (!b || inst < -1 || inst >= (int)b->cfgs.size()) return -1;
+  long long total = 0;
+  for (int i = 0; i < (int)b->cfgs.size(); ++i) {
+    if (inst >= 0 && i != inst) continue;
+    const es_config& C = b->cfgs[i];
+    total += (long long)C.nx * C.ny * C.nz * (C.p + 1) * (C.p + 1) * (C.p + 1);
+  }
+  return total;
+}
+
+int es_batch_node_coords(const es_batch* b, int inst, double* xyz_host) {
+  if (!b || !xyz_host || inst < 0 || inst >= (int)b->cfgs.size()) return ES_ERR_INVALID;
+  node_coords(b->cfgs[inst], xyz_host);
+  return ES_OK;
+}
+
+static int batch_copy(es_batch* b, int inst, double* host, bool to_device) {
+  if (!b || !host || inst < 0 || inst >= (int)b->cfgs.size()) return ES_ERR_INVALID;
+  const Group& g = b->groups[b->where[inst].first];
+  const InstGeom& G = g.geom[b->where[inst].second];
+  const long long Ki = (long long)G.nx * G.ny * G.nz;
+  const size_t bytes = sizeof(double) * Ki * g.Np;
+  int rc = cuda_check(cudaDeviceSynchronize());
+  for (int v = 0; v < 5 && rc == ES_OK; ++v) {
+    double* dev = g.q + v * g.N + (long long)G.off * g.Np;
+    double* hp = host + v * Ki * g.Np;
+    rc = cuda_check(to_device ? cudaMemcpy(dev, hp, bytes, cudaMemcpyHostToDevice)
+                              : cudaMemcpy(hp, dev, bytes, cudaMemcpyDeviceToHost));
+  }
+  return rc;
+}
+
+int es_batch_set_state(es_batch* b, int inst, const double* q_host) {
+  return batch_copy(b, inst, const_cast<double*>(q_host), true);
+}
+
+int es_batch_get_state(es_batch* b, int inst, double* q_host) { return batch_copy(b, inst, q_host, false); }
+
+int es_batch_set_dt(es_batch* b, const double* dt_host) {
+  if (!b || !dt_host) return ES_ERR_INVALID;
+  int rc = cuda_check(cudaDeviceSynchronize());
+  for (auto& g : b->groups) {
+    for (int j = 0; j < g.ninst && rc == ES_OK; ++j) {
+      const double dt = dt_host[g.inst_ids[j]];
+      if (!(dt > 0.0) || !std::isfinite(dt)) return ES_ERR_INVALID;
+      g.geom[j].dt = dt;
+    }
+    if (rc == ES_OK)
+      rc = cuda_check(cudaMemcpy(g.geom_dev, g.geom.data(), g.ninst * sizeof(InstGeom), cudaMemcpyHostToDevice));
+  }
+  return rc;
+}
+
+int es_batch_autotune(es_batch* b, void* stream) {
+  if (!b) return ES_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = ES_OK;
+  for (auto& g : b->groups) {
+    if (rc == ES_OK) rc = autotune_group(b->eng, g, g.q, st);
+  }
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return rc;
+}
+
+int es_batch_volume_variant(const es_batch* b, int inst) {
+  if (!b || inst < 0 || inst >= (int)b->cfgs.size()) return ES_ERR_INVALID;
+  return b->groups[b->where[inst].first].vol_variant;
+}
+
+int es_batch_advance(es_batch* b, int nsteps, void* stream) {
+  if (!b || nsteps < 0) return ES_ERR_INVALID;
+  for (auto& g : b->groups)
+    for (auto& G : g.geom)
+      if (!(G.dt > 0.0)) return ES_ERR_INVALID;  // es_batch_set_dt first
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Engine& E = b->eng;
+  int rc = ES_OK;
+  if (!b->exec) rc = batch_capture(b);
+  if (rc != ES_OK) return rc;
+  cudaEvent_t ev = nullptr;
+  rc = cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  if (rc == ES_OK) rc = cuda_check(cudaEventRecord(ev, st));
+  if (rc == ES_OK) rc = cuda_check(cudaStreamWaitEvent(b->exec_stream, ev, 0));
+  for (int n = 0; n < nsteps && rc == ES_OK; ++n) {
+    rc = cuda_check(cudaGraphLaunch(b->exec, b->exec_stream));
+    E.launches += b->kernels_per_step;
+  }
+  for (auto& g : b->groups)
+    if (rc == ES_OK && nsteps > 0) rc = group_finish(E, g, g.q, b->exec_stream);
+  if (rc == ES_OK) rc = cuda_check(cudaEventRecord(ev, b->exec_stream));
+  if (rc == ES_OK) rc = cuda_check(cudaStreamWaitEvent(st, ev, 0));
+  if (ev) cudaEventDestroy(ev);
+  return rc;
+}
+
+int es_batch_times(es_batch* b, double* t_host, double* gamma_host) {
+  if (!b) return ES_ERR_INVALID;
+  int rc = cuda_check(cudaDeviceSynchronize());
+  for (auto& g : b->groups) {
+    std::vector<double> t(g.ninst), gm(g.ninst);
+    if (rc == ES_OK) rc = cuda_check(cudaMemcpy(t.data(), g.t, g.ninst * sizeof(double), cudaMemcpyDeviceToHost));
+    if (rc == ES_OK)
+      rc = cuda_check(cudaMemcpy(gm.data(), g.gamma_cur, g.ninst * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int j = 0; j < g.ninst && rc == ES_OK; ++j) {
+      if (t_host) t_host[g.inst_ids[j]] = t[j];
+      if (gamma_host) gamma_host[g.inst_ids[j]] = gm[j];
+    }
+  }
+  return rc;
+}
+
+int es_batch_status(es_batch* b, void* stream) {
+  if (!b) return ES_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = cuda_check(cudaStreamSynchronize(b->exec_stream));
+  if (rc != ES_OK) return rc;
+  return status_read(b->eng, st);
+}
+
+long long es_batch_launch_count(const es_batch* b) { return b ? b->eng.launches : 0; }
+
+}  // extern "C"
+
 // ---------------------------------------------------------------------------
 // small kernels
 namespace {
 
-__global__ void k_scalar(unsigned long long* gmin_bits, double* gamma_cur, double* t, double* hist, int step,
-                         double dt, int relax) {
-  double g = __longlong_as_double((long long)*gmin_bits);
-  if (!relax || !(g < INFINITY)) g = 1.0;
-  *gamma_cur = g;
-  *t += g * dt;
-  if (hist) hist[step] = g;
-  *gmin_bits = 0x7ff0000000000000ULL;
+__global__ void k_scalar(int ninst, unsigned long long* gmin_bits, double* gamma_cur, double* t, double* hist,
+                         int* pending, const InstGeom* geom, double dt0, int relax) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x) {
+    double g = __longlong_as_double((long long)gmin_bits[i]);
+    if (!relax || !(g < INFINITY)) g = 1.0;
+    const double dt = geom ? geom[i].dt : dt0;
+    gamma_cur[i] = g;
+    t[i] += g * dt;
+    if (hist) hist[i] = g;
+    pending[i] = 1;
+    gmin_bits[i] = 0x7ff0000000000000ULL;
+  }
 }
 
-__global__ void k_reset_min(unsigned long long* gmin_bits) { *gmin_bits = 0x7ff0000000000000ULL; }
+__global__ void k_reset(unsigned long long* gmin_bits, int* pending, int ninst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x) {
+    gmin_bits[i] = 0x7ff0000000000000ULL;
+    pending[i] = 0;
+  }
+}
 
-// out = base + gamma d (out may alias base)
-__global__ void k_update(double* out, const double* base, const double* __restrict__ d,
-                         const double* __restrict__ gamma_cur, long long n) {
-  const double g = *gamma_cur;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = base[i] + g * d[i];
+// out = base + gamma[inst] d where the instance has a pending update (out may alias base)
+__global__ void k_update(Params P, double* out, const double* base, const double* __restrict__ d,
+                         const double* __restrict__ gamma_cur, const int* __restrict__ pending, int Np) {
+  const long long N = (long long)P.K * Np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 5 * N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int inst = inst_of(P, int((i % N) / Np));
+    if (pending[inst]) out[i] = base[i] + gamma_cur[inst] * d[i];
+    else if (out != base) out[i] = base[i];
+  }
 }
 
 }  // namespace
 
 namespace es {
-void launch_scalar(unsigned long long* gmin_bits, double* gamma_cur, double* t, double* hist, int step, double dt,
-                   int relax, cudaStream_t st) {
-  k_scalar<<<1, 1, 0, st>>>(gmin_bits, gamma_cur, t, hist, step, dt, relax);
+void launch_scalar(const Params& P, unsigned long long* gmin_bits, double* gamma_cur, double* t, double* hist,
+                   int* pending, int relax, cudaStream_t st) {
+  const int blocks = (P.ninst + 127) / 128;
+  k_scalar<<<blocks, 128, 0, st>>>(P.ninst, gmin_bits, gamma_cur, t, hist, pending, P.geom, P.g0.dt, relax);
 }
-void launch_reset_min(unsigned long long* gmin_bits, cudaStream_t st) { k_reset_min<<<1, 1, 0, st>>>(gmin_bits); }
-void launch_update(double* out, const double* base, const double* d, const double* gamma_cur, long long n,
-                   cudaStream_t st, int grid) {
-  k_update<<<grid, 256, 0, st>>>(out, base, d, gamma_cur, n);
+void launch_reset(unsigned long long* gmin_bits, int* pending, int ninst, cudaStream_t st) {
+  k_reset<<<(ninst + 127) / 128, 128, 0, st>>>(gmin_bits, pending, ninst);
+}
+void launch_update(const Params& P, double* out, const double* base, const double* d, const double* gamma_cur,
+                   const int* pending, int Np, cudaStream_t st, int grid) {
+  k_update<<<grid, 256, 0, st>>>(P, out, base, d, gamma_cur, pending, Np);
 }
 }  // namespace es

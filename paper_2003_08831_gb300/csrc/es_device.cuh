@@ -16,31 +16,48 @@ constexpr int kMaxP1 = 6;
 constexpr int kStatusNonphysical = 1;
 constexpr int kStatusNoRoot = 2;
 
+// Geometry of one periodic Cartesian instance (mesh) inside a group of
+// instances sharing the LGL degree; a single-instance context is a group of one.
+struct InstGeom {
+  int nx, ny, nz, off;  // element grid; first element of the instance in the group
+  double metric[3];     // 2/h_m
+  double J;             // h1 h2 h3 / 8
+  double dt;            // the instance's time step
+};
+
 // Operator tables and physics constants, passed by value to every kernel.
 struct Params {
   double D[kMaxP1 * kMaxP1];   // SBP derivative on [-1, 1], row-major
   double D2[kMaxP1 * kMaxP1];  // 2 D_ij (i != j), 0 on the diagonal
   double omega[kMaxP1];        // LGL weights
   double inv_omega_end;        // 1/omega_0 = 1/omega_p
-  double metric[3];            // 2/h_m
-  double J;                    // h1 h2 h3 / 8
   double gam;                  // ratio of specific heats
   double mu, kappa_heat, R;    // viscosity, heat conductivity mu c_p / Pr, gas constant
-  int nx, ny, nz, K;
+  int K;                       // elements in the group
   int diss;                    // Rusanov interface dissipation on/off
   int p1;                      // p + 1
+  int ninst;                   // instances in the group
+  InstGeom g0;                 // the instance when geom is null (single-instance context)
+  const InstGeom* geom;        // device table [ninst] (batches), or null
+  const int* elem_inst;        // device [K]: instance of each element (batches), or null
 };
 
 // ---------------------------------------------------------------------------
 // element / node index helpers
+__device__ __forceinline__ int inst_of(const Params& P, int e) { return P.elem_inst ? P.elem_inst[e] : 0; }
+
+__device__ __forceinline__ const InstGeom& geom_of(const Params& P, int inst) { return P.geom ? P.geom[inst] : P.g0; }
+
 __device__ __forceinline__ int neighbour(const Params& P, int e, int m, int dir) {
-  int ex = e % P.nx;
-  int ey = (e / P.nx) % P.ny;
-  int ez = e / (P.nx * P.ny);
-  if (m == 0) ex = (ex + dir + P.nx) % P.nx;
-  else if (m == 1) ey = (ey + dir + P.ny) % P.ny;
-  else ez = (ez + dir + P.nz) % P.nz;
-  return ex + P.nx * (ey + P.ny * ez);
+  const InstGeom& G = geom_of(P, inst_of(P, e));
+  const int le = e - G.off;
+  int ex = le % G.nx;
+  int ey = (le / G.nx) % G.ny;
+  int ez = le / (G.nx * G.ny);
+  if (m == 0) ex = (ex + dir + G.nx) % G.nx;
+  else if (m == 1) ey = (ey + dir + G.ny) % G.ny;
+  else ez = (ez + dir + G.nz) % G.nz;
+  return G.off + ex + G.nx * (ey + G.ny * ez);
 }
 
 // node index of position i on the line (a, b) in direction m
@@ -51,14 +68,15 @@ __device__ __forceinline__ int line_node(int m, int a, int b, int i) {
 
 // mass weight P_n = J omega_i omega_j omega_k
 template <int P1>
-__device__ __forceinline__ double mass_weight(const Params& P, int n) {
+__device__ __forceinline__ double mass_weight(const Params& P, double J, int n) {
   int i = n % P1, j = (n / P1) % P1, k = n / (P1 * P1);
-  return P.J * P.omega[i] * P.omega[j] * P.omega[k];
+  return J * P.omega[i] * P.omega[j] * P.omega[k];
 }
 
 // ---------------------------------------------------------------------------
 // Parameter-vector state used by the two-point flux: z = sqrt(rho/p) (1, v, p).
-constexpr int kAux = 5;
+constexpr int kAux = 5;       // planes read by the volume kernel
+constexpr int kAuxPlanes = 6; // + iz1 = 1/z1, read by the face kernel
 template <typename T>
 struct Zstate {
   T z[5];
@@ -73,56 +91,62 @@ template <typename T> struct LogMeanConst;
 template <> struct LogMeanConst<double> { static constexpr double eps = 1.0e-4; };
 template <> struct LogMeanConst<float> { static constexpr float eps = 1.0e-2f; };
 
-template <typename T>
-__device__ __forceinline__ T series_F(T u) {  // 1 + u/3 + u^2/5 + u^3/7
-  return T(1) + u * (T(1.0 / 3.0) + u * (T(1.0 / 5.0) + u * T(1.0 / 7.0)));
+// u >= 0 (a square) compared with a positive threshold on the integer pipe:
+// non-negative IEEE values order like their bit patterns (NaN compares false).
+__device__ __forceinline__ bool below(double u, double eps) {
+  return __double_as_longlong(u) < __double_as_longlong(eps);
 }
-template <typename T>
-__device__ __forceinline__ T series_invF(T u) {  // 1/F = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
-  return T(1) - u * (T(1.0 / 3.0) + u * (T(4.0 / 45.0) + u * T(44.0 / 945.0)));
-}
+__device__ __forceinline__ bool below(float u, float eps) { return __float_as_int(u) < __float_as_int(eps); }
 
 // Constants of the gas law used by the flux, in the flux's precision.
 template <typename T>
 struct FluxConst {
-  T gam, c1, c2, g_gm1, inv_gm1, sqrt_gam;
+  T gam, inv_gm1, sqrt_gam;
+  T C1x, C2x;  // 4 c1 gam/(gam-1), c2 gam/(gam-1) with c1 = (gam+1)/(2 gam), c2 = (gam-1)/(2 gam)
   __host__ __device__ static FluxConst make(double g) {
     FluxConst c;
     c.gam = T(g);
-    c.c1 = T((g + 1.0) / (2.0 * g));
-    c.c2 = T((g - 1.0) / (2.0 * g));
-    c.g_gm1 = T(g / (g - 1.0));
     c.inv_gm1 = T(1.0 / (g - 1.0));
     c.sqrt_gam = T(sqrt(g));
+    c.C1x = T(4.0 * (g + 1.0) / (2.0 * g) * g / (g - 1.0));
+    c.C2x = T((g - 1.0) / (2.0 * g) * g / (g - 1.0));
     return c;
   }
 };
 
 // Ismail--Roe two-point flux in direction m between states a and b.
+// With S = a + b, D = a - b for z1 and z5, the two logarithmic means enter only
+// through f1 = S1/(2 ln-mean(z1)) and g5 = ln-mean(z5)/(2 S5):
+//   rho_hat = z1_avg ln-mean(z5) = S1 S5 g5,   u_hat = (z_{2..4} sums)/S1,
+//   p1_hat = S5/S1,   p2_hat = p1_hat (4 c1 g5 f1 + c2),
+//   flux_m = (rho_hat u_m, rho_hat u_m u_hat + p1_hat e_m,
+//             u_m gam/(gam-1) p2_hat + rho_hat u_m |u_hat|^2/2).
+// Series branch (u = (D/S)^2 below the threshold): f1 = F(u1), g5 = (1/F)(u5)/4 with
+// F(u) = 1 + u/3 + u^2/5 + u^3/7 and 1/F = 1 - u/3 - 4u^2/45 - 44u^3/945;
+// otherwise f1 = S1 ln(a/b)/(2 D1), g5 = D5/(2 S5 ln(a/b)).
 template <typename T>
 __device__ __forceinline__ void ec_flux(const Zstate<T>& a, const Zstate<T>& b, int m, const FluxConst<T>& C,
                                         T f[5]) {
   const T S1 = a.z[0] + b.z[0], D1 = a.z[0] - b.z[0];
   const T S5 = a.z[4] + b.z[4], D5 = a.z[4] - b.z[4];
-  const T inv = T(1) / (S1 * S5);
+  const T P15 = S1 * S5;
+  const T inv = T(1) / P15;
   const T inv1 = S5 * inv;          // 1/S1
   const T r1 = D1 * inv1;
   const T r5 = D5 * (S1 * inv);     // D5/S5
   const T u1 = r1 * r1, u5 = r5 * r5;
   const T eps = LogMeanConst<T>::eps;
-  // 1 / ln-mean(z1) and ln-mean(z5)
-  T inv_lm1, lm5;
-  if (u1 < eps) inv_lm1 = T(2) * series_F(u1) * inv1;
-  else inv_lm1 = log(a.z[0] / b.z[0]) / D1;
-  if (u5 < eps) lm5 = T(0.5) * S5 * series_invF(u5);
-  else lm5 = D5 / log(a.z[4] / b.z[4]);
-  const T zb1 = T(0.5) * S1;
-  const T rho_hat = zb1 * lm5;
+  T f1, g5;
+  if (below(u1, eps)) f1 = T(1) + u1 * (T(1.0 / 3.0) + u1 * (T(1.0 / 5.0) + u1 * T(1.0 / 7.0)));
+  else f1 = T(0.5) * S1 * log(a.z[0] / b.z[0]) / D1;
+  if (below(u5, eps)) g5 = T(0.25) - u5 * (T(1.0 / 12.0) + u5 * (T(1.0 / 45.0) + u5 * T(11.0 / 945.0)));
+  else g5 = T(0.5) * D5 / (S5 * log(a.z[4] / b.z[4]));
+  const T rho_hat = P15 * g5;
   const T u0 = (a.z[1] + b.z[1]) * inv1;
   const T uy = (a.z[2] + b.z[2]) * inv1;
   const T uz = (a.z[3] + b.z[3]) * inv1;
   const T p1 = S5 * inv1;
-  const T p2 = C.c1 * lm5 * inv_lm1 + C.c2 * p1;
+  const T p2g = p1 * (C.C1x * (g5 * f1) + C.C2x);  // gam/(gam-1) p2_hat
   const T um = m == 0 ? u0 : (m == 1 ? uy : uz);
   const T mass = rho_hat * um;
   const T q2 = u0 * u0 + uy * uy + uz * uz;
@@ -131,15 +155,14 @@ __device__ __forceinline__ void ec_flux(const Zstate<T>& a, const Zstate<T>& b, 
   f[2] = mass * uy;
   f[3] = mass * uz;
   f[1 + m] += p1;
-  // rho_hat u_m h_hat with h_hat = gam p2/((gam-1) rho_hat) + |u|^2/2
-  f[4] = um * C.g_gm1 * p2 + T(0.5) * mass * q2;
+  f[4] = um * p2g + (T(0.5) * mass) * q2;
 }
 
-// Conserved state from the parameter vector: rho = z1 z5, v = z_{2..4}/z1,
-// p = z5/z1, c = sqrt(gam)/z1.
+// Conserved state from the parameter vector and iz1 = 1/z1 = sqrt(p/rho):
+// rho = z1 z5, v = z_{2..4}/z1, p = z5/z1, c = sqrt(gam)/z1.
 template <typename T>
-__device__ __forceinline__ void z_to_q(const Zstate<T>& s, const FluxConst<T>& C, T q[5], T& vn_abs_plus_c, int m) {
-  const T iz1 = T(1) / s.z[0];
+__device__ __forceinline__ void z_to_q(const Zstate<T>& s, T iz1, const FluxConst<T>& C, T q[5], T& vn_abs_plus_c,
+                                       int m) {
   const T rho = s.z[0] * s.z[4];
   const T v0 = s.z[1] * iz1, v1 = s.z[2] * iz1, v2 = s.z[3] * iz1;
   const T p = s.z[4] * iz1;

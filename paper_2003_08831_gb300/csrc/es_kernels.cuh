@@ -23,12 +23,23 @@
 
 namespace es {
 
-// elements per CTA of the volume kernel and its thread count
-template <int P1> struct VolCfg;
-template <> struct VolCfg<3> { static constexpr int EPB = 32, THREADS = 288; };
-template <> struct VolCfg<4> { static constexpr int EPB = 8, THREADS = 128; };
-template <> struct VolCfg<5> { static constexpr int EPB = 5, THREADS = 128; };
-template <> struct VolCfg<6> { static constexpr int EPB = 4, THREADS = 160; };
+// Volume-kernel tiles: elements per CTA (EPB) and threads per CTA for each degree.
+// A CTA handles EPB (p+1)^2 lines per direction; the candidates are chosen so the
+// lines fill whole warps or nearly so.  Variant 0 is the default; the batch
+// autotuner times all of them on the instance data and keeps the fastest.
+template <int P1, int V> struct VolCfg;
+template <> struct VolCfg<3, 0> { static constexpr int EPB = 32, THREADS = 288; };
+template <> struct VolCfg<3, 1> { static constexpr int EPB = 16, THREADS = 160; };
+template <> struct VolCfg<3, 2> { static constexpr int EPB = 8, THREADS = 96; };
+template <> struct VolCfg<4, 0> { static constexpr int EPB = 8, THREADS = 128; };
+template <> struct VolCfg<4, 1> { static constexpr int EPB = 4, THREADS = 64; };
+template <> struct VolCfg<4, 2> { static constexpr int EPB = 16, THREADS = 256; };
+template <> struct VolCfg<5, 0> { static constexpr int EPB = 5, THREADS = 128; };
+template <> struct VolCfg<5, 1> { static constexpr int EPB = 10, THREADS = 256; };
+template <> struct VolCfg<5, 2> { static constexpr int EPB = 2, THREADS = 64; };
+template <> struct VolCfg<6, 0> { static constexpr int EPB = 4, THREADS = 160; };
+template <> struct VolCfg<6, 1> { static constexpr int EPB = 2, THREADS = 96; };
+template <> struct VolCfg<6, 2> { static constexpr int EPB = 8, THREADS = 288; };
 
 // ---------------------------------------------------------------------------
 // accurate w(u + e) - w(u) from the increment e (no cancellation):
@@ -67,16 +78,19 @@ __device__ __forceinline__ void entropy_var_increment(const double u[5], const d
 }
 
 // ---------------------------------------------------------------------------
-template <typename TF>
+// y = u (+ gamma d when the instance has a pending relaxed update and this is the
+// step's first stage) + dt sum_j a_ij k_j; NPREV stages enter (compile time).
+template <typename TF, int NPREV>
 __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __restrict__ status) {
   const long long N = (long long)P.K * sp.Np;
   const double gam = P.gam;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    const int inst = inst_of(P, int(g / sp.Np));
     double u[5], y[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = sp.q[v * N + g];
-    if (sp.apply_update) {
-      const double gmm = *sp.gamma_cur;
+    if (sp.pending && sp.pending[inst]) {
+      const double gmm = sp.gamma_cur[inst];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         u[v] = u[v] + gmm * sp.d[v * N + g];
@@ -85,11 +99,15 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) y[v] = u[v];
-    for (int j = 0; j < sp.nprev; ++j) {
-      const double c = sp.coef[j];
-      const double* kj = sp.k[j];
+    if constexpr (NPREV > 0) {
+      const double dt = geom_of(P, inst).dt;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) y[v] = fma(c, kj[v * N + g], y[v]);
+      for (int j = 0; j < NPREV; ++j) {
+        const double c = sp.coef[j] * dt;
+        const double* kj = sp.k[j];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) y[v] = fma(c, kj[v * N + g], y[v]);
+      }
     }
     const double rho = y[0];
     const double ir = 1.0 / rho;
@@ -105,6 +123,7 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
       aux[2 * N + g] = z1 * v1;
       aux[3 * N + g] = z1 * v2;
       aux[4 * N + g] = rho * p * rs;
+      aux[5 * N + g] = p * rs;  // 1/z1 = sqrt(p/rho)
     } else {
       const float rf = float(rho), pf = float(p);
       const float rs = rsqrtf(rf * pf);
@@ -114,6 +133,7 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
       aux[2 * N + g] = z1 * float(v1);
       aux[3 * N + g] = z1 * float(v2);
       aux[4 * N + g] = rf * pf * rs;
+      aux[5 * N + g] = pf * rs;
     }
     if (sp.dw) {
       double e[5], dw[5];
@@ -148,14 +168,16 @@ __global__ void k_face(Params P, const TF* __restrict__ aux, TF* __restrict__ F)
     const int e = int(rem / P2), ab = int(rem % P2);
     const int a = ab % P1, b = ab / P1;
     const int en = neighbour(P, e, m, +1);
-    const Zstate<TF> L = load_z<P1, TF>(aux, N, (long long)e * Np + line_node<P1>(m, a, b, P1 - 1));
-    const Zstate<TF> R = load_z<P1, TF>(aux, N, (long long)en * Np + line_node<P1>(m, a, b, 0));
+    const long long gL = (long long)e * Np + line_node<P1>(m, a, b, P1 - 1);
+    const long long gR = (long long)en * Np + line_node<P1>(m, a, b, 0);
+    const Zstate<TF> L = load_z<P1, TF>(aux, N, gL);
+    const Zstate<TF> R = load_z<P1, TF>(aux, N, gR);
     TF f[5];
     ec_flux(L, R, m, C, f);
     if (P.diss) {
       TF qL[5], qR[5], lL, lR;
-      z_to_q(L, C, qL, lL, m);
-      z_to_q(R, C, qR, lR, m);
+      z_to_q(L, aux[5 * N + gL], C, qL, lL, m);
+      z_to_q(R, aux[5 * N + gR], C, qR, lR, m);
       const TF lam = TF(0.5) * fmax(lL, lR);
 #pragma unroll
       for (int v = 0; v < 5; ++v) f[v] -= lam * (qR[v] - qL[v]);
@@ -205,7 +227,7 @@ __global__ void k_grad(Params P, const TF* __restrict__ aux, TF* __restrict__ fV
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[c] += sg * (wn[c] - ws[c]);
       }
-      const TF met = TF(P.metric[m]);
+      const TF met = TF(geom_of(P, inst_of(P, e)).metric[m]);
 #pragma unroll
       for (int c = 0; c < 4; ++c) th[m][c] = met * acc[c];
     }
@@ -240,11 +262,10 @@ __global__ void k_grad(Params P, const TF* __restrict__ aux, TF* __restrict__ fV
 }
 
 // ---------------------------------------------------------------------------
-template <int P1, typename TF, bool NS>
-__global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageVol sv, const TF* __restrict__ aux,
-                                                             const TF* __restrict__ F, const TF* __restrict__ fV) {
+template <int P1, typename TF, bool NS, int EPB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const TF* __restrict__ aux,
+                                                   const TF* __restrict__ F, const TF* __restrict__ fV) {
   constexpr int P2 = P1 * P1, Np = P1 * P2;
-  constexpr int EPB = VolCfg<P1>::EPB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TF* za = reinterpret_cast<TF*>(smem_raw);            // [kAux][EPB*Np]
   TF* acc = za + kAux * EPB * Np;                       // [5][EPB*Np]
@@ -264,11 +285,11 @@ __global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageV
 
 #pragma unroll 1
   for (int m = 0; m < 3; ++m) {
-    const TF met = TF(P.metric[m]);
     for (int l = threadIdx.x; l < nel * P2; l += blockDim.x) {
       const int el = l / P2, ab = l % P2;
       const int a = ab % P1, b = ab / P1;
       const int e = e0 + el;
+      const TF met = TF(geom_of(P, inst_of(P, e)).metric[m]);
       Zstate<TF> z[P1];
 #pragma unroll
       for (int i = 0; i < P1; ++i) {
@@ -343,21 +364,23 @@ __global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageV
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
     const long long g = (long long)e0 * Np + t;
     const int n = t % Np;
+    const InstGeom& G = geom_of(P, inst_of(P, e0 + t / Np));
     double k[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) k[v] = double(acc[v * EPB * Np + t]);
     if (sv.d_out) {
+      const double dt = G.dt;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        double dv = sv.dcoef_self * k[v];
-        for (int j = 0; j < sv.nd; ++j) dv = fma(sv.dcoef[j], sv.dk[j][v * N + g], dv);
+        double dv = (sv.dcoef_self * dt) * k[v];
+        for (int j = 0; j < sv.nd; ++j) dv = fma(sv.dcoef[j] * dt, sv.dk[j][v * N + g], dv);
         sv.d_out[v * N + g] = dv;
       }
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) sv.kout[v * N + g] = k[v];
     }
-    const double Pn = mass_weight<P1>(P, n);
+    const double Pn = mass_weight<P1>(P, G.J, n);
     if (wantE) {
       Zstate<TF> s;
 #pragma unroll
@@ -373,7 +396,7 @@ __global__ void __launch_bounds__(VolCfg<P1>::THREADS) k_volume(Params P, StageV
       double sum = 0.0;
 #pragma unroll
       for (int v = 0; v < 5; ++v) sum += sv.dw[v * N + g] * k[v];
-      red[EPB * Np + t] = Pn * sum;
+      red[EPB * Np + t] = Pn * G.dt * sum;
     }
   }
   const bool doA = sv.A != nullptr && (wantA || sv.A_init);
@@ -415,6 +438,8 @@ __global__ void k_relax(Params P, StageRelax sr) {
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
   for (int e = blockIdx.x * warps_per_block + (threadIdx.x >> 5); e < P.K; e += gridDim.x * warps_per_block) {
+    const int inst = inst_of(P, e);
+    const double J = geom_of(P, inst).J;
     RelaxNode nd[R];
     double a_part = 0.0, s_part = 0.0, A_part = 0.0;
 #pragma unroll
@@ -446,7 +471,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
         const double v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
         const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
         const double dv0 = (d[1] - v0 * d[0]) * ir, dv1 = (d[2] - v1 * d[0]) * ir, dv2 = (d[3] - v2 * d[0]) * ir;
-        const double Pn = mass_weight<P1>(P, n);
+        const double Pn = mass_weight<P1>(P, J, n);
         nd[r].X0 = d[0] * ir;
         nd[r].Y0 = (gam - 1.0) * (d[4] - (v0 * d[1] + v1 * d[2] + v2 * d[3]) + 0.5 * v2s * d[0]) * ip;
         nd[r].V2 = rho * (dv0 * dv0 + dv1 * dv1 + dv2 * dv2) * ip;
@@ -529,7 +554,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
     }
     if (lane == 0) {
       sr.gamma_elem[e] = gk;
-      atomic_min_positive(sr.gmin_bits, gk);
+      atomic_min_positive(sr.gmin_bits + inst, gk);
     }
   }
 }
@@ -543,6 +568,7 @@ __global__ void k_entropy(Params P, const double* __restrict__ q, double* __rest
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < P.K; e += gridDim.x * wpb) {
+    const double J = geom_of(P, inst_of(P, e)).J;
     double s = 0.0;
     for (int n = lane; n < Np; n += 32) {
       const long long g = (long long)e * Np + n;
@@ -550,7 +576,7 @@ __global__ void k_entropy(Params P, const double* __restrict__ q, double* __rest
       const double ir = 1.0 / rho;
       const double m0 = q[N + g], m1 = q[2 * N + g], m2 = q[3 * N + g];
       const double p = (gam - 1.0) * (q[4 * N + g] - 0.5 * (m0 * m0 + m1 * m1 + m2 * m2) * ir);
-      s += mass_weight<P1>(P, n) * (-rho * (log(p) - gam * log(rho)) / (gam - 1.0));
+      s += mass_weight<P1>(P, J, n) * (-rho * (log(p) - gam * log(rho)) / (gam - 1.0));
     }
     s = warp_sum(s);
     if (lane == 0) eta[e] = s;
@@ -562,7 +588,13 @@ __global__ void k_entropy(Params P, const double* __restrict__ q, double* __rest
 template <int P1, typename TF>
 void Launcher<P1, TF>::prep(const Params& P, const StagePrep& sp, void* aux, int* status, cudaStream_t st,
                             int grid) {
-  k_prep<TF><<<grid, 256, 0, st>>>(P, sp, static_cast<TF*>(aux), status);
+  TF* a = static_cast<TF*>(aux);
+  switch (sp.nprev) {
+    case 0: k_prep<TF, 0><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+    case 1: k_prep<TF, 1><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+    case 2: k_prep<TF, 2><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+    default: k_prep<TF, 3><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+  }
 }
 
 template <int P1, typename TF>
@@ -575,31 +607,51 @@ void Launcher<P1, TF>::grad(const Params& P, const void* aux, void* fV, cudaStre
   k_grad<P1, TF><<<grid, 256, 0, st>>>(P, static_cast<const TF*>(aux), static_cast<TF*>(fV));
 }
 
-template <int P1, typename TF>
-size_t Launcher<P1, TF>::volume_smem() {
-  constexpr int Np = P1 * P1 * P1;
-  return size_t(VolCfg<P1>::EPB) * Np * ((kAux + 5) * sizeof(TF) + 2 * sizeof(double));
+template <int P1, int EPB>
+constexpr size_t vol_smem_bytes(size_t tf) {
+  return size_t(EPB) * P1 * P1 * P1 * ((kAux + 5) * tf + 2 * sizeof(double));
 }
 
-template <int P1, typename TF>
-cudaError_t Launcher<P1, TF>::volume_setup() {
-  cudaError_t e1 = cudaFuncSetAttribute(k_volume<P1, TF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)volume_smem());
-  cudaError_t e2 = cudaFuncSetAttribute(k_volume<P1, TF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)volume_smem());
+template <int P1, typename TF, int V>
+cudaError_t volume_setup_v() {
+  using C = VolCfg<P1, V>;
+  const int smem = (int)vol_smem_bytes<P1, C::EPB>(sizeof(TF));
+  cudaError_t e1 = cudaFuncSetAttribute(k_volume<P1, TF, false, C::EPB, C::THREADS>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e2 = cudaFuncSetAttribute(k_volume<P1, TF, true, C::EPB, C::THREADS>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e1 != cudaSuccess ? e1 : e2;
 }
 
 template <int P1, typename TF>
-void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* aux, const void* F, const void* fV,
-                              bool ns, cudaStream_t st) {
-  const int grid = (P.K + VolCfg<P1>::EPB - 1) / VolCfg<P1>::EPB;
+cudaError_t Launcher<P1, TF>::volume_setup() {
+  cudaError_t e = volume_setup_v<P1, TF, 0>();
+  if (e == cudaSuccess) e = volume_setup_v<P1, TF, 1>();
+  if (e == cudaSuccess) e = volume_setup_v<P1, TF, 2>();
+  return e;
+}
+
+template <int P1, typename TF, int V>
+void volume_v(const Params& P, const StageVol& sv, const TF* aux, const TF* F, const TF* fV, bool ns,
+              cudaStream_t st) {
+  using C = VolCfg<P1, V>;
+  const int grid = (P.K + C::EPB - 1) / C::EPB;
+  const size_t smem = vol_smem_bytes<P1, C::EPB>(sizeof(TF));
   if (ns)
-    k_volume<P1, TF, true><<<grid, VolCfg<P1>::THREADS, volume_smem(), st>>>(
-        P, sv, static_cast<const TF*>(aux), static_cast<const TF*>(F), static_cast<const TF*>(fV));
+    k_volume<P1, TF, true, C::EPB, C::THREADS><<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, fV);
   else
-    k_volume<P1, TF, false><<<grid, VolCfg<P1>::THREADS, volume_smem(), st>>>(
-        P, sv, static_cast<const TF*>(aux), static_cast<const TF*>(F), static_cast<const TF*>(fV));
+    k_volume<P1, TF, false, C::EPB, C::THREADS><<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, fV);
+}
+
+template <int P1, typename TF>
+void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* aux, const void* F, const void* fV,
+                              bool ns, cudaStream_t st, int variant) {
+  const TF* a = static_cast<const TF*>(aux);
+  const TF* f = static_cast<const TF*>(F);
+  const TF* v = static_cast<const TF*>(fV);
+  if (variant == 1) volume_v<P1, TF, 1>(P, sv, a, f, v, ns, st);
+  else if (variant == 2) volume_v<P1, TF, 2>(P, sv, a, f, v, ns, st);
+  else volume_v<P1, TF, 0>(P, sv, a, f, v, ns, st);
 }
 
 template <int P1, typename TF>

@@ -10,17 +10,18 @@ namespace es {
 
 // host helpers shared by the entry points (es_api.cu)
 int validate_config(const es_config& C);
+InstGeom instance_geom(const es_config& C, int off);
 void build_params(const es_config& C, Params* out);
 int grid_for_sms(int sm_count, long long n, int block);
 
-// k_prep: stage state y = u (+ gamma d first) + sum_j coef[j] k[j]
+// k_prep: stage state y = u (+ gamma d first) + dt sum_j coef[j] k[j]
 struct StagePrep {
-  double* q;                // u, updated in place when apply_update
-  const double* d;          // previous step's increment (apply_update)
-  const double* gamma_cur;  // device scalar (apply_update)
-  int apply_update;
+  double* q;                // u, updated in place when an update is pending
+  const double* d;          // previous step's increment
+  const double* gamma_cur;  // per instance: gamma of the previous step
+  const int* pending;       // per instance: relaxed update u += gamma d not yet applied (nullptr: none)
   int nprev;
-  double coef[4];           // dt a_ij
+  double coef[4];           // a_ij (multiplied by the instance's dt in the kernel)
   const double* k[4];
   double* dw;               // w(y) - w(u) output, or nullptr
   int Np;
@@ -29,15 +30,15 @@ struct StagePrep {
 // k_volume outputs
 struct StageVol {
   double* kout;        // k_i = f(y^i) (unless d_out is set)
-  double* d_out;       // last stage: d = dcoef_self k_i + sum_j dcoef[j] dk[j] instead of k_i
+  double* d_out;       // last stage: d = dt (dcoef_self k_i + sum_j dcoef[j] dk[j]) instead of k_i
   int nd;
-  double dcoef[4];
+  double dcoef[4];     // b_j
   const double* dk[4];
-  double dcoef_self;
+  double dcoef_self;   // b_i
   double* E;           // (eta' f)(y^i) per element, or nullptr
   const double* dw;    // w(y^i) - w(u), or nullptr
   double* A;           // relaxation term accumulator, or nullptr
-  double A_scale;      // -dt b_i
+  double A_scale;      // -b_i (times the instance's dt in the kernel)
   int A_init;          // first stage of the step: A starts at zero
 };
 
@@ -50,32 +51,34 @@ struct StageRelax {
   const double* A;         // accumulated A (RK mode)
   double* d_out;           // u_new mode: d written here
   double* gamma_elem;
-  unsigned long long* gmin_bits;
+  unsigned long long* gmin_bits;  // per instance
   int* status;
   double delta_floor;
   double gamma_max;
 };
+
+constexpr int kVolumeVariants = 3;
 
 template <int P1, typename TF>
 struct Launcher {
   static void prep(const Params& P, const StagePrep& sp, void* aux, int* status, cudaStream_t st, int grid);
   static void face(const Params& P, const void* aux, void* F, cudaStream_t st, int grid);
   static void grad(const Params& P, const void* aux, void* fV, cudaStream_t st, int grid);
-  static size_t volume_smem();
   static cudaError_t volume_setup();
+  // variant: volume tile (elements per CTA, threads), 0..kVolumeVariants-1
   static void volume(const Params& P, const StageVol& sv, const void* aux, const void* F, const void* fV, bool ns,
-                     cudaStream_t st);
+                     cudaStream_t st, int variant);
   static void relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid);
   static void entropy(const Params& P, const double* q, double* eta, cudaStream_t st, int grid);
 };
 
-// scalar step bookkeeping: gamma = min gamma_kappa (or 1), t += gamma dt,
-// hist[step] = gamma, reset of the min accumulator
-void launch_scalar(unsigned long long* gmin_bits, double* gamma_cur, double* t, double* hist, int step, double dt,
-                   int relax, cudaStream_t st);
-// out = base + gamma d over n values (out may alias base)
-void launch_update(double* out, const double* base, const double* d, const double* gamma_cur, long long n,
-                   cudaStream_t st, int grid);
-void launch_reset_min(unsigned long long* gmin_bits, cudaStream_t st);
+// per-instance step bookkeeping: gamma = min gamma_kappa (or 1), t += gamma dt,
+// hist[i] = gamma (if hist), pending[i] = 1, reset of the min accumulator
+void launch_scalar(const Params& P, unsigned long long* gmin_bits, double* gamma_cur, double* t, double* hist,
+                   int* pending, int relax, cudaStream_t st);
+// out = base + gamma[inst] d over the group's 5 K Np values where pending[inst] (out may alias base)
+void launch_update(const Params& P, double* out, const double* base, const double* d, const double* gamma_cur,
+                   const int* pending, int Np, cudaStream_t st, int grid);
+void launch_reset(unsigned long long* gmin_bits, int* pending, int ninst, cudaStream_t st);
 
 }  // namespace es

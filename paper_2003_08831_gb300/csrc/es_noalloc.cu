@@ -74,7 +74,7 @@ extern "C" size_t es_rhs_noalloc_scratch_bytes(const es_config* cfg) {
   const size_t K = size_t(cfg->nx) * cfg->ny * cfg->nz;
   const size_t N = K * P1 * P1 * P1;
   size_t b = align256(sizeof(int));
-  b += align256(kAux * N * tf);
+  b += align256(kAuxPlanes * N * tf);
   b += align256(15 * K * P1 * P1 * tf);
   if (cfg->mu > 0.0) b += align256(12 * N * tf);
   return b;
@@ -105,7 +105,7 @@ extern "C" int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqd
   int* status = reinterpret_cast<int*>(base);
   size_t off = align256(sizeof(int));
   void* aux = base + off;
-  off += align256(kAux * size_t(N) * tf);
+  off += align256(kAuxPlanes * size_t(N) * tf);
   void* F = base + off;
   off += align256(15 * size_t(K) * P1 * P1 * tf);
   void* fV = cfg->mu > 0.0 ? static_cast<void*>(base + off) : nullptr;
@@ -126,7 +126,7 @@ extern "C" int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqd
     Lc::prep(P, sp, aux, status, st, grid_for_sms(sms, N, 256));
     Lc::face(P, aux, F, st, grid_for_sms(sms, 3LL * K * P1 * P1, 256));
     if (ns) Lc::grad(P, aux, fV, st, grid_for_sms(sms, N, 256));
-    Lc::volume(P, sv, aux, F, fV, ns, st);
+    Lc::volume(P, sv, aux, F, fV, ns, st, 0);
     return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
   });
   return rc;

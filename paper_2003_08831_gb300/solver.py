@@ -89,6 +89,9 @@ class Solver:
     def launch_count(self):
         return B.es_launch_count(self.ctx)
 
+    def autotune(self, q, stream=None):
+        B.es_autotune(self.ctx, q, stream)
+
     def profile(self, enable):
         B.es_profile_enable(self.ctx, enable)
 
@@ -111,3 +114,72 @@ def stable_dt(q, p, h, cfl, gamma_gas=1.4, mu=0.0, Pr=0.72):
         k2 = sum(((2 * p + 1) / h[m]) ** 2 for m in range(3))
         dt = min(dt, cfl * float(np.min(rho)) / (mu * max(4.0 / 3.0, gamma_gas / Pr) * k2))
     return dt
+
+
+class BatchSolver:
+    """Many independent instances (possibly different degrees and element counts)."""
+
+    def __init__(self, instances, gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0, interface_diss=1,
+                 relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64, delta_floor=1e-8):
+        """instances: list of dicts with p, n (nx, ny, nz), lo, hi."""
+        self.cfgs = [B.make_config(d["p"], d["n"], d.get("lo", (0.0, 0.0, 0.0)), d.get("hi", (1.0, 1.0, 1.0)),
+                                   gamma_gas, mu, Pr, R, interface_diss, relax, rk, precision, delta_floor)
+                     for d in instances]
+        self.instances = instances
+        self.count = len(instances)
+        self.b = B.es_batch_create(self.cfgs)
+
+    def close(self):
+        if self.b is not None:
+            B.es_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, i):
+        d = self.instances[i]
+        P1 = d["p"] + 1
+        return (5, d["n"][0] * d["n"][1] * d["n"][2], P1 ** 3)
+
+    def nodes(self, i=-1):
+        return B.es_batch_nodes(self.b, i)
+
+    def coords(self, i):
+        sh = self.shape(i)
+        xyz = np.empty((3, sh[1], sh[2]))
+        B.es_batch_node_coords(self.b, i, xyz)
+        return xyz
+
+    def set_state(self, i, q):
+        q = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(self.shape(i)))
+        B.es_batch_set_state(self.b, i, q)
+
+    def get_state(self, i):
+        q = np.empty(self.shape(i))
+        B.es_batch_get_state(self.b, i, q)
+        return q
+
+    def set_dt(self, dt):
+        B.es_batch_set_dt(self.b, np.ascontiguousarray(np.asarray(dt, dtype=np.float64)))
+
+    def autotune(self, stream=None):
+        B.es_batch_autotune(self.b, stream)
+
+    def advance(self, nsteps, stream=None):
+        B.es_batch_advance(self.b, nsteps, stream)
+
+    def times(self):
+        t = np.zeros(self.count)
+        g = np.zeros(self.count)
+        B.es_batch_times(self.b, t, g)
+        return t, g
+
+    def status(self, stream=None):
+        return B.es_batch_status(self.b, stream)
+
+    def launch_count(self):
+        return B.es_batch_launch_count(self.b)
