@@ -430,6 +430,10 @@ int group_init(Group& g, const es_config* insts, int n, int stages, bool own_sta
     g.P.geom = g.geom_dev;
     g.P.elem_inst = g.elem_inst_dev;
   }
+  if (rc == ES_OK) {  // gamma accumulators start at +inf, no update pending
+    launch_reset(g.gmin, g.pending, n, nullptr);
+    rc = cuda_check(cudaDeviceSynchronize());
+  }
   if (rc == ES_OK) rc = dispatch(g, [&](auto L) { return cuda_check(decltype(L)::volume_setup()); });
   return rc;
 }
