@@ -66,7 +66,8 @@ typedef struct {
   int precision;        /* ES_FP64 or ES_MIXED */
   double delta_floor;   /* elements whose RMS relative change over the step is
                            <= delta_floor are unconstrained (gamma_kappa = +inf);
-                           <= 0 selects 1e-8 */
+                           <= 0 selects 1e-8 (ES_FP64) or 4e-6 (ES_MIXED: 64 eps_32,
+                           above the FP32 right-hand side's rounding noise) */
 } es_config;
 
 /* Mesh, LGL/SBP tables (Section 3.1: diagonal-norm SBP on LGL nodes) and

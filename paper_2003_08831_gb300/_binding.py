@@ -158,7 +158,7 @@ def _stream(stream):
 
 
 def make_config(p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0,
-                interface_diss=1, relax=ES_RELAX_LOCAL, rk=ES_RK_BS3, precision=ES_FP64, delta_floor=1e-8):
+                interface_diss=1, relax=ES_RELAX_LOCAL, rk=ES_RK_BS3, precision=ES_FP64, delta_floor=0.0):
     c = es_config()
     c.p = p
     c.nx, c.ny, c.nz = n

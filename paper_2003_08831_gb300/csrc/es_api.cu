@@ -469,7 +469,12 @@ StageRelax relax_base(Engine& E, Group& g) {
   sr.gamma_elem = g.gamma_elem;
   sr.gmin_bits = g.gmin;
   sr.status = E.status;
-  sr.delta_floor = g.cfg.delta_floor > 0.0 ? g.cfg.delta_floor : 1e-8;
+  // default floor: FP64 right-hand sides are exact to ~1e-15 of the state per step, so
+  // 1e-8 leaves a wide margin; FP32 right-hand sides carry rounding noise of relative size
+  // ~eps_32 times the flux-to-state cancellation, and below 64 eps_32 ~ 4e-6 an element's
+  // relaxation would be fitted to that noise.
+  const double floor_default = g.cfg.precision == ES_MIXED ? 4e-6 : 1e-8;
+  sr.delta_floor = g.cfg.delta_floor > 0.0 ? g.cfg.delta_floor : floor_default;
   sr.gamma_max = 8.0;
   return sr;
 }

@@ -189,15 +189,35 @@ __global__ void k_face(Params P, const TF* __restrict__ aux, TF* __restrict__ F)
 
 // ---------------------------------------------------------------------------
 // BR1 gradients and viscous flux per node.  fV[(m*4 + c) N + g], c = momentum
-// x, y, z, energy.  theta_m = (2/h_m) [D w + (1/omega) (w_face_avg - w) n_m].
-template <int P1, typename TF>
-__global__ void k_grad(Params P, const TF* __restrict__ aux, TF* __restrict__ fV) {
+// x, y, z, energy.  theta_m = (2/h_m) [D w + (1/omega) (w_face_avg - w) n_m] for
+// w_2..w_5 (the viscous flux needs no other component).  A CTA stages the
+// entropy variables of its EPB elements in shared memory once; neighbours'
+// face values come from global memory.
+template <int P1, typename TF, int EPB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_grad(Params P, const TF* __restrict__ aux, TF* __restrict__ fV) {
   constexpr int P2 = P1 * P1, Np = P1 * P2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TF* ws = reinterpret_cast<TF*>(smem_raw);  // [4][EPB*Np]
   const long long N = (long long)P.K * Np;
-  const TF mu = TF(P.mu), kap = TF(P.kappa_heat), Rg = TF(P.R);
+  const int e0 = blockIdx.x * EPB;
+  const int nel = min(EPB, P.K - e0);
+  const int nn = nel * Np;
+  const TF mu = TF(P.mu), kap = TF(P.kappa_heat), iR = TF(1.0 / P.R);
   const TF iw = TF(P.inv_omega_end);
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
-    const int e = int(g / Np), n = int(g % Np);
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+    const long long g = (long long)e0 * Np + t;
+    const TF z1 = aux[g];
+    ws[0 * EPB * Np + t] = z1 * aux[N + g];
+    ws[1 * EPB * Np + t] = z1 * aux[2 * N + g];
+    ws[2 * EPB * Np + t] = z1 * aux[3 * N + g];
+    ws[3 * EPB * Np + t] = -z1 * z1;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int el = t / Np, n = t % Np;
+    const int e = e0 + el;
+    const long long g = (long long)e0 * Np + t;
+    const InstGeom& G = geom_of(P, inst_of(P, e));
     const int ii[3] = {n % P1, (n / P1) % P1, n / P2};
     TF th[3][4];
 #pragma unroll
@@ -208,42 +228,35 @@ __global__ void k_grad(Params P, const TF* __restrict__ aux, TF* __restrict__ fV
       TF acc[4] = {TF(0), TF(0), TF(0), TF(0)};
 #pragma unroll
       for (int j = 0; j < P1; ++j) {
-        const Zstate<TF> s = load_z<P1, TF>(aux, N, (long long)e * Np + line_node<P1>(m, a, b, j));
-        TF w[4];
-        z_to_wv(s, w);
+        const int nj = el * Np + line_node<P1>(m, a, b, j);
         const TF Dij = TF(P.D[im * P1 + j]);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] += Dij * w[c];
+        for (int c = 0; c < 4; ++c) acc[c] += Dij * ws[c * EPB * Np + nj];
       }
       if (im == P1 - 1 || im == 0) {
         const bool right = (im == P1 - 1);
         const int en = neighbour(P, e, m, right ? +1 : -1);
-        const Zstate<TF> sn = load_z<P1, TF>(aux, N, (long long)en * Np + line_node<P1>(m, a, b, right ? 0 : P1 - 1));
-        const Zstate<TF> ss = load_z<P1, TF>(aux, N, g);
-        TF wn[4], ws[4];
-        z_to_wv(sn, wn);
-        z_to_wv(ss, ws);
+        const long long gn = (long long)en * Np + line_node<P1>(m, a, b, right ? 0 : P1 - 1);
+        const TF zn1 = aux[gn];
+        const TF wn[4] = {zn1 * aux[N + gn], zn1 * aux[2 * N + gn], zn1 * aux[3 * N + gn], -zn1 * zn1};
         const TF sg = right ? TF(0.5) * iw : TF(-0.5) * iw;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] += sg * (wn[c] - ws[c]);
+        for (int c = 0; c < 4; ++c) acc[c] += sg * (wn[c] - ws[c * EPB * Np + t]);
       }
-      const TF met = TF(geom_of(P, inst_of(P, e)).metric[m]);
+      const TF met = TF(G.metric[m]);
 #pragma unroll
       for (int c = 0; c < 4; ++c) th[m][c] = met * acc[c];
     }
-    // chain rule: v = -w_{2..4}/w_5, T = -1/(R w_5)
-    const Zstate<TF> s = load_z<P1, TF>(aux, N, g);
-    const TF z1 = s.z[0];
-    const TF iz1 = TF(1) / z1;
-    const TF v[3] = {s.z[1] * iz1, s.z[2] * iz1, s.z[3] * iz1};
-    const TF w5 = -z1 * z1;
-    const TF iw5 = TF(1) / w5;
+    // chain rule: v = -w_{2..4}/w_5 = z_{2..4}/z1, T = -1/(R w_5)
+    const TF iz1 = aux[5 * N + g];
+    const TF v[3] = {aux[N + g] * iz1, aux[2 * N + g] * iz1, aux[3 * N + g] * iz1};
+    const TF iw5 = -iz1 * iz1;  // 1/w_5
     TF gv[3][3], gT[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) gv[m][k] = -(th[m][k] + v[k] * th[m][3]) * iw5;
-      gT[m] = th[m][3] * iw5 * iw5 / Rg;
+      gT[m] = th[m][3] * iw5 * iw5 * iR;
     }
     const TF divv = gv[0][0] + gv[1][1] + gv[2][2];
 #pragma unroll
@@ -426,8 +439,9 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
 // r'(g) = sum_n c dD_n/dg + A; a = r''(0)/2 = sum c (X0^2 + (X0-Y0)^2/(gam-1) + V2)/2.
 // Newton from the root -A/a of the quadratic model, safeguarded by the bracket
 // [lo, hi] (r(lo) <= 0 < r(hi)); r is convex, so Newton converges from above.
-// A step |s| <= 1e-9 g leaves an error ~ s^2/g below 1e-18 g: the updated
-// iterate is returned without another evaluation.
+// Near the root the error after a step s is ~ s^2 r''/(2 r') ~ s^2/g, so a step
+// |s| <= 1e-8 g leaves an error ~1e-16 g: the updated iterate is returned
+// without another evaluation.
 template <int P1>
 __global__ void k_relax(Params P, StageRelax sr) {
   constexpr int Np = P1 * P1 * P1;
@@ -534,7 +548,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
           const double step = rv / dv;
           const double newton = gcur - step;
           const bool nok = phys && dv > 0.0 && isfinite(newton) && newton > lo && newton < hi;
-          if (nok && fabs(step) <= 1e-9 * gcur) {
+          if (nok && fabs(step) <= 1e-8 * gcur) {
             gk = newton;
             break;
           }
@@ -603,8 +617,12 @@ void Launcher<P1, TF>::face(const Params& P, const void* aux, void* F, cudaStrea
 }
 
 template <int P1, typename TF>
-void Launcher<P1, TF>::grad(const Params& P, const void* aux, void* fV, cudaStream_t st, int grid) {
-  k_grad<P1, TF><<<grid, 256, 0, st>>>(P, static_cast<const TF*>(aux), static_cast<TF*>(fV));
+void Launcher<P1, TF>::grad(const Params& P, const void* aux, void* fV, cudaStream_t st, int) {
+  using C = VolCfg<P1, 0>;
+  const int grid = (P.K + C::EPB - 1) / C::EPB;
+  const size_t smem = size_t(4) * C::EPB * P1 * P1 * P1 * sizeof(TF);
+  k_grad<P1, TF, C::EPB, C::THREADS><<<grid, C::THREADS, smem, st>>>(P, static_cast<const TF*>(aux),
+                                                                      static_cast<TF*>(fV));
 }
 
 template <int P1, int EPB>

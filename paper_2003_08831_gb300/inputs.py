@@ -46,11 +46,19 @@ def conserved(rho, vx, vy, vz, p, gamma):
                      p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz)])
 
 
-def vortex_primitives(x, y, t=0.0, eps=5.0, mach=0.5, gamma=1.4, alpha=np.pi / 4, centre=(0.0, 0.0)):
-    """(rho, u1, u2, u3, p) of the isentropic vortex at time t."""
+def vortex_primitives(x, y, t=0.0, eps=5.0, mach=0.5, gamma=1.4, alpha=np.pi / 4, centre=(0.0, 0.0),
+                      period=None):
+    """(rho, u1, u2, u3, p) of the isentropic vortex at time t.
+
+    With period = L the offsets from the (moving) centre are taken to the nearest
+    periodic image (minimum-image convention), so a vortex placed anywhere in a
+    periodic box of side L is continuous up to its tail at distance L/2."""
     uinf = 1.0
     dx = (x - centre[0]) - uinf * np.cos(alpha) * t
     dy = (y - centre[1]) - uinf * np.sin(alpha) * t
+    if period is not None:
+        dx = np.mod(dx + 0.5 * period, period) - 0.5 * period
+        dy = np.mod(dy + 0.5 * period, period) - 0.5 * period
     G = 1.0 - (dx * dx + dy * dy)
     T = 1.0 - eps * eps * mach * mach * (gamma - 1.0) / (8.0 * np.pi ** 2) * np.exp(G)
     rho = T ** (1.0 / (gamma - 1.0))
@@ -61,8 +69,8 @@ def vortex_primitives(x, y, t=0.0, eps=5.0, mach=0.5, gamma=1.4, alpha=np.pi / 4
     return rho, u1, u2, np.zeros_like(rho), p
 
 
-def vortex_state(x, y, t=0.0, eps=5.0, mach=0.5, gamma=1.4, alpha=np.pi / 4, centre=(0.0, 0.0)):
-    rho, u1, u2, u3, p = vortex_primitives(x, y, t, eps, mach, gamma, alpha, centre)
+def vortex_state(x, y, t=0.0, eps=5.0, mach=0.5, gamma=1.4, alpha=np.pi / 4, centre=(0.0, 0.0), period=None):
+    rho, u1, u2, u3, p = vortex_primitives(x, y, t, eps, mach, gamma, alpha, centre, period)
     return conserved(rho, u1, u2, u3, p, gamma)
 
 
@@ -98,7 +106,8 @@ def batch_instances(count=256, seed=SEED, nmin=4, nmax=12, pmin=2, pmax=5, box=1
 
     Each instance i draws, from counters 8 i + 0..5: n in {nmin..nmax} (n^3
     elements), p in {pmin..pmax}, vortex centre in [0, box]^2, strength in
-    [3, 6] and background Mach number in [0.1, 0.5].
+    [3, 6] and background Mach number in [0.1, 0.5].  The instance's initial
+    state is vortex_state(..., period=box): the centre can be anywhere.
     """
     out = []
     for i in range(count):

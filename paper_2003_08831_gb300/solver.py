@@ -12,7 +12,7 @@ from . import _binding as B
 class Solver:
     def __init__(self, p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0,
                  interface_diss=1, relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64,
-                 delta_floor=1e-8, device="cuda"):
+                 delta_floor=0.0, device="cuda"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -120,7 +120,7 @@ class BatchSolver:
     """Many independent instances (possibly different degrees and element counts)."""
 
     def __init__(self, instances, gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0, interface_diss=1,
-                 relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64, delta_floor=1e-8):
+                 relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64, delta_floor=0.0):
         """instances: list of dicts with p, n (nx, ny, nz), lo, hi."""
         self.cfgs = [B.make_config(d["p"], d["n"], d.get("lo", (0.0, 0.0, 0.0)), d.get("hi", (1.0, 1.0, 1.0)),
                                    gamma_gas, mu, Pr, R, interface_diss, relax, rk, precision, delta_floor)

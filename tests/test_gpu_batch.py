@@ -33,7 +33,8 @@ def instances(count, seed=11):
 
 
 def initial(inst, x, y):
-    return inputs.vortex_state(x, y, 0.0, eps=inst["eps"], mach=inst["mach"], centre=inst["centre"])
+    return inputs.vortex_state(x, y, 0.0, eps=inst["eps"], mach=inst["mach"], centre=inst["centre"],
+                               period=inst["hi"][0] - inst["lo"][0])
 
 
 def oracle_run(inst, nsteps):

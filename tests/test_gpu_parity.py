@@ -397,3 +397,51 @@ def test_mixed_advance_error(case):
     err = rel_l2(q.cpu().numpy(), Uo)
     assert np.all(err < 1e-5), err
     s.close()
+
+
+# ---------------------------------------------------------------------------------------
+# Section 4.4 (Eq. visu_of_local_gamma): the 1D smooth + discontinuous case as a
+# 200 x 1 x 1 periodic mesh, RK(4,4), dt = 1e-4.
+
+def x6_state(mesh):
+    x, _, _ = mesh.coords()
+    left = x < 0
+    rho = np.where(left, 1 + 0.5 * np.cos(2 * np.pi * x), 0.5 + 0.25 * np.cos(2 * np.pi * x))
+    u = np.full_like(x, 0.5)
+    pr = np.where(left, 1.0, 0.8)
+    return inputs.conserved(rho, u, 0 * u, 0 * u, pr, G)
+
+
+def test_local_gamma_variation_x6():
+    """Parity with the oracle over the first 20 steps, then the paper's printed bound
+    |gamma_kappa - 1| < 2e-5 at t = 0.1 (tests/golden/local_gamma_variation.txt)."""
+    import os
+    from paper_2003_08831_gb300 import _binding as B
+    gold = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "local_gamma_variation.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split("=")
+                gold[k.strip()] = float(v)
+    K = int(gold["elements"])
+    lo, hi = (-2.0, 0.0, 0.0), (2.0, 4.0 / K, 4.0 / K)
+    mesh = dg.Mesh(int(gold["p"]), (K, 1, 1), lo, hi)
+    U = x6_state(mesh)
+    phys = dg.Physics(G, diss=1)
+    dt = gold["dt"]
+    Uo, to, hist = rk.advance(mesh, U, dt, 20, phys, rk.RK4)
+    s = solver(mesh.p, mesh.n, lo, hi, rk=B.ES_RK_RK4)
+    q = s.to_device(U)
+    t, gh, gk = s.advance(q, 20, dt)
+    assert s.status() == 0
+    err = rel_err_per_var(q.cpu().numpy(), Uo)
+    assert np.all(err < TOL), err
+    steps = int(round(gold["t_final"] / dt))
+    t, gh, gk = s.advance(q, steps - 20, dt, t)
+    assert s.status() == 0
+    g = gk.cpu().numpy()
+    g = g[np.isfinite(g)]
+    assert g.size > 0
+    assert np.max(np.abs(g - 1.0)) < gold["bound"], np.max(np.abs(g - 1.0))
+    s.close()
