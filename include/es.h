@@ -49,6 +49,8 @@ extern "C" {
 
 #define ES_RELAX_NONE 0  /* baseline RK, gamma = 1 */
 #define ES_RELAX_LOCAL 1 /* gamma = min_kappa gamma_kappa (Theorem 2.3) */
+#define ES_RELAX_GLOBAL 2 /* one gamma per instance for eta = sum_kappa eta_kappa
+                             (Eqs. (u-n-gamma), (t-n-gamma)); gamma_elem reports it */
 
 typedef struct es_ctx es_ctx;
 
@@ -201,6 +203,12 @@ int es_batch_times(es_batch* b, double* t_host, double* gamma_host);
 int es_batch_status(es_batch* b, void* stream);
 /* kernels enqueued (graph replays count every kernel of the step) */
 long long es_batch_launch_count(const es_batch* b);
+
+/* out[i] = 1/x[i] (device arrays) with the library's FP64 reciprocal: the
+ * hardware approximation refined by two Newton--Raphson steps, used in the
+ * flux, thermodynamics and relaxation kernels in place of IEEE division.
+ * Exposed so that it can be checked against IEEE division; x must be normal. */
+int es_reciprocal(const double* x, double* out, long long n, void* stream);
 
 /* Static message for an ES_* code. */
 const char* es_strerror(int code);

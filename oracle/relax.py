@@ -183,13 +183,16 @@ def solve_gamma(u, d, A, P, g, delta_floor=DELTA_FLOOR, gamma_max=GAMMA_MAX, max
         hi[idx] = np.where(pos, gi, hi[idx])
         di = sub.dr(gi)
         with np.errstate(divide="ignore", invalid="ignore"):
-            newton = gi - ri / di
+            step_n = ri / di
+            newton = gi - step_n
+        tol = TOL * np.maximum(1.0, gi)
+        # a Newton step below the tolerance has converged even when rounding puts the
+        # iterate on an end of the bracket
+        newton_conv = (~nonphys) & (di > 0.0) & np.isfinite(newton) & (np.abs(step_n) <= tol)
         ok = (~nonphys) & np.isfinite(newton) & (newton > lo[idx]) & (newton < hi[idx])
         nxt = np.where(ok, newton, 0.5 * (lo[idx] + hi[idx]))
-        step = np.abs(nxt - gi)
-        tol = TOL * np.maximum(1.0, gi)
-        conv = (ok & (step <= tol)) | ((hi[idx] - lo[idx]) <= tol) | (ri == 0.0)
-        gam[idx] = np.where(conv & ok, nxt, np.where(conv, gi, nxt))
+        conv = newton_conv | ((hi[idx] - lo[idx]) <= tol) | (ri == 0.0)
+        gam[idx] = np.where(newton_conv, np.clip(newton, lo[idx], hi[idx]), np.where(conv, gi, nxt))
         done[idx] = conv
     gam = np.where(capped, gamma_max, gam)
     gam_k[act] = gam

@@ -20,7 +20,7 @@ ES_ERR_NOMEM = -6
 ES_ERR_TOO_LARGE = -7
 ES_RK_BS3, ES_RK_RK4 = 0, 1
 ES_FP64, ES_MIXED = 0, 1
-ES_RELAX_NONE, ES_RELAX_LOCAL = 0, 1
+ES_RELAX_NONE, ES_RELAX_LOCAL, ES_RELAX_GLOBAL = 0, 1, 2
 
 EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "es_advance",
            "es_advance_host", "es_node_coords", "es_status", "es_launch_count", "es_strerror",
@@ -28,7 +28,7 @@ EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "
            "es_autotune", "es_batch_create", "es_batch_destroy", "es_batch_nodes", "es_batch_node_coords",
            "es_batch_set_state", "es_batch_get_state", "es_batch_set_dt", "es_batch_autotune",
            "es_batch_volume_variant", "es_batch_advance", "es_batch_times", "es_batch_status",
-           "es_batch_launch_count"]
+           "es_batch_launch_count", "es_reciprocal"]
 KERNEL_KINDS = ["prep", "face", "grad", "volume", "relax", "other"]
 
 
@@ -115,6 +115,8 @@ def load(path=None):
     lib.es_batch_status.restype = i
     lib.es_batch_launch_count.argtypes = [vp]
     lib.es_batch_launch_count.restype = ctypes.c_longlong
+    lib.es_reciprocal.argtypes = [vp, vp, ctypes.c_longlong, vp]
+    lib.es_reciprocal.restype = i
     lib.es_strerror.argtypes = [i]
     lib.es_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -303,3 +305,7 @@ def es_batch_status(b, stream=None):
 
 def es_batch_launch_count(b):
     return int(load().es_batch_launch_count(b))
+
+
+def es_reciprocal(x, out, stream=None):
+    _check(load().es_reciprocal(_ptr(x), _ptr(out), int(x.numel()), _stream(stream)), "es_reciprocal")

@@ -117,7 +117,7 @@ int validate_config(const es_config& C) {
   if (!(C.gamma_gas > 1.0) || !(C.R > 0.0) || C.mu < 0.0 || (C.mu > 0.0 && !(C.Pr > 0.0))) return ES_ERR_INVALID;
   if (C.rk != ES_RK_BS3 && C.rk != ES_RK_RK4) return ES_ERR_INVALID;
   if (C.precision != ES_FP64 && C.precision != ES_MIXED) return ES_ERR_INVALID;
-  if (C.relax != ES_RELAX_NONE && C.relax != ES_RELAX_LOCAL) return ES_ERR_INVALID;
+  if (C.relax != ES_RELAX_NONE && C.relax != ES_RELAX_LOCAL && C.relax != ES_RELAX_GLOBAL) return ES_ERR_INVALID;
   if (C.interface_diss != 0 && C.interface_diss != 1) return ES_ERR_INVALID;
   for (int m = 0; m < 3; ++m)
     if (!(C.hi[m] > C.lo[m])) return ES_ERR_INVALID;
@@ -209,6 +209,8 @@ struct Group {
   int* pending = nullptr;                // [ninst]
   double* t = nullptr;                   // [ninst] (batch)
   double* q = nullptr;                   // group-owned state (batch)
+  double* gwork = nullptr;               // global relaxation: [4][K] element sums
+  GlobalRelaxState* gstate = nullptr;    // global relaxation: [ninst]
   InstGeom* geom_dev = nullptr;
   int* elem_inst_dev = nullptr;
 };
@@ -371,6 +373,8 @@ void group_free(Group& g) {
   cudaFree(g.pending);
   cudaFree(g.t);
   cudaFree(g.q);
+  cudaFree(g.gwork);
+  cudaFree(g.gstate);
   cudaFree(g.geom_dev);
   cudaFree(g.elem_inst_dev);
   g = Group();
@@ -413,6 +417,9 @@ int group_init(Group& g, const es_config* insts, int n, int stages, bool own_sta
   if (rc == ES_OK) rc = dev_alloc(&g.pending, n);
   if (rc == ES_OK) rc = dev_alloc(&g.t, n);
   if (rc == ES_OK && own_state) rc = dev_alloc(&g.q, 5 * N);
+  if (rc == ES_OK && C.relax == ES_RELAX_GLOBAL) rc = dev_alloc(&g.gwork, 4 * K);
+  if (rc == ES_OK && C.relax == ES_RELAX_GLOBAL) rc = dev_alloc(&g.gstate, n);
+  if (rc == ES_OK && C.relax == ES_RELAX_GLOBAL) rc = cuda_check(cudaMemset(g.gstate, 0, n * sizeof(GlobalRelaxState)));
   if (rc == ES_OK) rc = cuda_check(cudaMemset(g.pending, 0, n * sizeof(int)));
   if (rc == ES_OK) rc = cuda_check(cudaMemset(g.gamma_cur, 0, n * sizeof(double)));
   if (rc == ES_OK) rc = cuda_check(cudaMemset(g.t, 0, n * sizeof(double)));
@@ -485,7 +492,7 @@ StageRelax relax_base(Engine& E, Group& g) {
 // hist (device, per instance) receives gamma if not null.
 int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStream_t st) {
   const Tableau& T = E.tab;
-  const bool relax = E.relax == ES_RELAX_LOCAL;
+  const bool relax = E.relax != ES_RELAX_NONE;
   int rc = ES_OK;
   for (int i = 0; i < T.s && rc == ES_OK; ++i) {
     StagePrep sp;
@@ -526,11 +533,36 @@ int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStre
   }
   if (rc != ES_OK) return rc;
   StageRelax sr = relax_base(E, g);
-  sr.u = q;
-  sr.d_in = g.d;
-  sr.A = g.A;
-  if (!relax) sr.delta_floor = INFINITY;  // every element unconstrained: gamma = 1
-  rc = run_relax(E, g, sr, st);
+  if (E.relax == ES_RELAX_GLOBAL) {
+    GlobalRelaxArgs ga;
+    std::memset(&ga, 0, sizeof(ga));
+    ga.u = q;
+    ga.d = g.d;
+    ga.A = g.A;
+    ga.nodes = g.dw;  // free after the last stage
+    ga.elem_a = g.gwork;
+    ga.elem_s = g.gwork + g.K;
+    ga.elem_r = g.gwork + 2 * (long long)g.K;
+    ga.elem_dr = g.gwork + 3 * (long long)g.K;
+    ga.gs = g.gstate;
+    ga.gmin_bits = g.gmin;
+    ga.gamma_elem = g.gamma_elem;
+    ga.status = E.status;
+    ga.delta_floor = sr.delta_floor;
+    ga.gamma_max = sr.gamma_max;
+    const int grid = (int)std::min<long long>((g.K + 3) / 4, (long long)E.sm_count * 16);
+    rc = dispatch(g, [&](auto L) {
+      timed(E, ES_KERNEL_RELAX, st,
+            [&] { decltype(L)::global_relax(g.P, ga, st, grid, kGlobalRelaxIterations); });
+      return last_launch_error();
+    });
+  } else {
+    sr.u = q;
+    sr.d_in = g.d;
+    sr.A = g.A;
+    if (!relax) sr.delta_floor = INFINITY;  // every element unconstrained: gamma = 1
+    rc = run_relax(E, g, sr, st);
+  }
   if (rc != ES_OK) return rc;
   timed(E, ES_KERNEL_OTHER, st, [&] { launch_scalar(g.P, g.gmin, g.gamma_cur, t, hist, g.pending, relax ? 1 : 0, st); });
   return last_launch_error();
@@ -1048,11 +1080,18 @@ int es_batch_status(es_batch* b, void* stream) {
 
 long long es_batch_launch_count(const es_batch* b) { return b ? b->eng.launches : 0; }
 
+int es_reciprocal(const double* x, double* out, long long n, void* stream);
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
 // small kernels
 namespace {
+
+__global__ void k_reciprocal(const double* __restrict__ x, double* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = fast_rcp(x[i]);
+}
 
 __global__ void k_scalar(int ninst, unsigned long long* gmin_bits, double* gamma_cur, double* t, double* hist,
                          int* pending, const InstGeom* geom, double dt0, int relax) {
@@ -1088,6 +1127,16 @@ __global__ void k_update(Params P, double* out, const double* base, const double
 }
 
 }  // namespace
+
+extern "C" int es_reciprocal(const double* x, double* out, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return ES_ERR_INVALID;
+  if (n == 0) return ES_OK;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return ES_ERR_CUDA;
+  k_reciprocal<<<grid_for_sms(sms, n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n);
+  return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
+}
 
 namespace es {
 void launch_scalar(const Params& P, unsigned long long* gmin_bits, double* gamma_cur, double* t, double* hist,

@@ -91,6 +91,26 @@ template <typename T> struct LogMeanConst;
 template <> struct LogMeanConst<double> { static constexpr double eps = 1.0e-4; };
 template <> struct LogMeanConst<float> { static constexpr float eps = 1.0e-2f; };
 
+// 1/x for FP64 without the IEEE division sequence: the hardware approximation
+// (PTX rcp.approx.ftz.f64) refined by two Newton--Raphson steps r <- r + r (1 - x r),
+// each doubling the number of correct bits.  x must be a normal positive or
+// negative number (subnormals flush to zero); the result is within a few units
+// in the last place of 1/x, not correctly rounded.
+__device__ __forceinline__ double fast_rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ float fast_rcp(float x) { return 1.0f / x; }
+
+// |z| <= t for a positive threshold t, on the integer pipe (sign bit cleared)
+__device__ __forceinline__ bool abs_le(double z, double t) {
+  return (__double_as_longlong(z) & 0x7fffffffffffffffLL) <= __double_as_longlong(t);
+}
+
 // u >= 0 (a square) compared with a positive threshold on the integer pipe:
 // non-negative IEEE values order like their bit patterns (NaN compares false).
 __device__ __forceinline__ bool below(double u, double eps) {
@@ -130,7 +150,7 @@ __device__ __forceinline__ void ec_flux(const Zstate<T>& a, const Zstate<T>& b, 
   const T S1 = a.z[0] + b.z[0], D1 = a.z[0] - b.z[0];
   const T S5 = a.z[4] + b.z[4], D5 = a.z[4] - b.z[4];
   const T P15 = S1 * S5;
-  const T inv = T(1) / P15;
+  const T inv = fast_rcp(P15);
   const T inv1 = S5 * inv;          // 1/S1
   const T r1 = D1 * inv1;
   const T r5 = D5 * (S1 * inv);     // D5/S5
@@ -201,7 +221,7 @@ __device__ __forceinline__ void z_to_w(const Zstate<T>& s, const FluxConst<T>& C
 //   |t| < 0.053 and eight terms of the even series reach 1e-17 relative.
 // otherwise the direct difference (cancellation costs at most a factor 20).
 __device__ __forceinline__ double log1pmx(double z) {
-  if (fabs(z) <= 1e-3) {
+  if (abs_le(z, 1e-3)) {
     double s = 1.0 / 7.0;
     s = fma(s, z, -1.0 / 6.0);
     s = fma(s, z, 1.0 / 5.0);
@@ -210,8 +230,8 @@ __device__ __forceinline__ double log1pmx(double z) {
     s = fma(s, z, -0.5);
     return z * z * s;
   }
-  if (fabs(z) <= 0.1) {
-    const double t = z / (2.0 + z);
+  if (abs_le(z, 0.1)) {
+    const double t = z * fast_rcp(2.0 + z);
     const double t2 = t * t;
     double s = 1.0 / 17.0;
     s = s * t2 + 1.0 / 15.0;
@@ -249,7 +269,7 @@ __device__ __forceinline__ bool relax_node_eval(const RelaxNode& nd, double g, d
   const double Yb = g * nd.Y0 * opx - (gam - 1.0) * K0;
   const double opy_n = opx + Yb;  // (1+y)(1+x)
   if (!(opx > 0.0) || !(opy_n > 0.0)) return false;
-  const double inv = 1.0 / (opx * opy_n);
+  const double inv = fast_rcp(opx * opy_n);
   const double q = opy_n * inv;        // 1/(1+x)
   const double iy = opx * opx * inv;   // 1/(1+y)
   const double y = Yb * q;

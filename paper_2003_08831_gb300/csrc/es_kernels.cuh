@@ -56,7 +56,7 @@ __device__ __forceinline__ void entropy_var_increment(const double u[5], const d
   const double rho1 = rho + e[0];
   const double m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
   const double Pr = (gam - 1.0) * (rho * u[4] - 0.5 * m2);
-  const double inv = 1.0 / (rho * rho1 * Pr);
+  const double inv = fast_rcp(rho * rho1 * Pr);
   const double ir = rho1 * Pr * inv, ir1 = rho * Pr * inv, ip = rho * rho * rho1 * inv;
   const double v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
   const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
@@ -66,7 +66,7 @@ __device__ __forceinline__ void entropy_var_increment(const double u[5], const d
   const double y =
       (gam - 1.0) * (e[4] - (v0 * e[1] + v1 * e[2] + v2 * e[3]) + 0.5 * v2s * e[0] - 0.5 * rho1 * dv2) * ip;
   const double beta = rho * ip;
-  const double iy = 1.0 / (1.0 + y);
+  const double iy = fast_rcp(1.0 + y);
   const double ds = (y + log1pmx(y)) - gam * (x + log1pmx(x));
   const double xy = x - y;
   const double dkin = 0.5 * beta * (xy * v2s + (1.0 + x) * (2.0 * (v0 * d0 + v1 * d1 + v2 * d2) + dv2)) * iy;
@@ -110,7 +110,7 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
       }
     }
     const double rho = y[0];
-    const double ir = 1.0 / rho;
+    const double ir = fast_rcp(rho);
     const double v0 = y[1] * ir, v1 = y[2] * ir, v2 = y[3] * ir;
     const double p = (gam - 1.0) * (y[4] - 0.5 * rho * (v0 * v0 + v1 * v1 + v2 * v2));
     if (!(rho > 0.0) || !(p > 0.0)) atomicOr(status, kStatusNonphysical);
@@ -480,7 +480,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
         const double rho = u[0];
         const double m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
         const double Pr = (gam - 1.0) * (rho * u[4] - 0.5 * m2);
-        const double inv = 1.0 / (rho * Pr);
+        const double inv = fast_rcp(rho * Pr);
         const double ir = Pr * inv, ip = rho * rho * inv;
         const double v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
         const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
@@ -547,11 +547,12 @@ __global__ void k_relax(Params P, StageRelax sr) {
           }
           const double step = rv / dv;
           const double newton = gcur - step;
-          const bool nok = phys && dv > 0.0 && isfinite(newton) && newton > lo && newton < hi;
-          if (nok && fabs(step) <= 1e-8 * gcur) {
-            gk = newton;
+          // converged: a step this small cannot leave the bracket by more than rounding
+          if (phys && dv > 0.0 && fabs(step) <= 1e-8 * gcur) {
+            gk = fmin(fmax(newton, lo), hi);
             break;
           }
+          const bool nok = phys && dv > 0.0 && isfinite(newton) && newton > lo && newton < hi;
           if (hi - lo <= 8.881784197001252e-16 * fmax(1.0, gcur)) {  // 4 * 2^-52
             gk = lo;
             break;
@@ -570,6 +571,194 @@ __global__ void k_relax(Params P, StageRelax sr) {
       sr.gamma_elem[e] = gk;
       atomic_min_positive(sr.gmin_bits + inst, gk);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Global relaxation (Eqs. (u-n-gamma), (t-n-gamma); the comparison mode of the
+// paper): one root per instance of r(g) = sum_kappa r_kappa(g).  Node data are
+// stored once; every Newton iteration evaluates per-element sums at the
+// instance's current gamma and one block per instance reduces them in a fixed
+// order (deterministic) and takes the Newton/bisection step.
+
+// per node (X0, Y0, V2, c) into nodes[4][N]; per element a_kappa and sum c
+template <int P1>
+__global__ void k_gsetup(Params P, const double* __restrict__ u, const double* __restrict__ d,
+                         double* __restrict__ nodes, double* __restrict__ elem_a, double* __restrict__ elem_s) {
+  constexpr int Np = P1 * P1 * P1;
+  const long long N = (long long)P.K * Np;
+  const double gam = P.gam, inv_gm1 = 1.0 / (gam - 1.0);
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < P.K; e += gridDim.x * wpb) {
+    const double J = geom_of(P, inst_of(P, e)).J;
+    double a_part = 0.0, s_part = 0.0;
+    for (int n = lane; n < Np; n += 32) {
+      const long long g = (long long)e * Np + n;
+      const double rho = u[g], m0 = u[N + g], m1 = u[2 * N + g], m2 = u[3 * N + g], E = u[4 * N + g];
+      const double Pr = (gam - 1.0) * (rho * E - 0.5 * (m0 * m0 + m1 * m1 + m2 * m2));
+      const double inv = 1.0 / (rho * Pr);
+      const double ir = Pr * inv, ip = rho * rho * inv;
+      const double v0 = m0 * ir, v1 = m1 * ir, v2 = m2 * ir;
+      const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
+      const double d0 = d[g], d1 = d[N + g], d2 = d[2 * N + g], d3 = d[3 * N + g], d4 = d[4 * N + g];
+      const double dv0 = (d1 - v0 * d0) * ir, dv1 = (d2 - v1 * d0) * ir, dv2 = (d3 - v2 * d0) * ir;
+      const double X0 = d0 * ir;
+      const double Y0 = (gam - 1.0) * (d4 - (v0 * d1 + v1 * d2 + v2 * d3) + 0.5 * v2s * d0) * ip;
+      const double V2 = rho * (dv0 * dv0 + dv1 * dv1 + dv2 * dv2) * ip;
+      const double c = mass_weight<P1>(P, J, n) * rho;
+      nodes[g] = X0;
+      nodes[N + g] = Y0;
+      nodes[2 * N + g] = V2;
+      nodes[3 * N + g] = c;
+      const double XY = X0 - Y0;
+      a_part += 0.5 * c * (X0 * X0 + XY * XY * inv_gm1 + V2);
+      s_part += c;
+    }
+    a_part = warp_sum(a_part);
+    s_part = warp_sum(s_part);
+    if (lane == 0) {
+      elem_a[e] = a_part;
+      elem_s[e] = s_part;
+    }
+  }
+}
+
+// per element sum_n c D_n(g)/rho_n and its g-derivative at the instance's gamma (NaN if not physical)
+template <int P1>
+__global__ void k_geval(Params P, const double* __restrict__ nodes, const GlobalRelaxState* __restrict__ gs,
+                        double* __restrict__ elem_r, double* __restrict__ elem_dr) {
+  constexpr int Np = P1 * P1 * P1;
+  const long long N = (long long)P.K * Np;
+  const double gam = P.gam, inv_gm1 = 1.0 / (gam - 1.0);
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < P.K; e += gridDim.x * wpb) {
+    const GlobalRelaxState& S = gs[inst_of(P, e)];
+    if (S.done) continue;
+    const double gcur = S.g;
+    double r = 0.0, dr = 0.0;
+    bool ok = true;
+    for (int n = lane; n < Np; n += 32) {
+      const long long g = (long long)e * Np + n;
+      RelaxNode nd;
+      nd.X0 = nodes[g];
+      nd.Y0 = nodes[N + g];
+      nd.V2 = nodes[2 * N + g];
+      nd.c = nodes[3 * N + g];
+      double D, dD;
+      if (relax_node_eval(nd, gcur, gam, inv_gm1, D, dD)) {
+        r += nd.c * D;
+        dr += nd.c * dD;
+      } else {
+        ok = false;
+      }
+    }
+    const bool phys = __all_sync(0xffffffffu, ok);
+    r = warp_sum(r);
+    dr = warp_sum(dr);
+    if (lane == 0) {
+      elem_r[e] = phys ? r : __longlong_as_double(0x7ff8000000000000LL);
+      elem_dr[e] = dr;
+    }
+  }
+}
+
+// fixed-order block reduction of x[off .. off+n) (all threads get the sum)
+__device__ inline double block_sum(const double* x, int off, int n, double* sh) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[off + i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double out = sh[0];
+  __syncthreads();
+  return out;
+}
+
+// one block per instance.  phase 0: totals, degenerate / no-root checks, initial
+// gamma; phase 1: one safeguarded Newton step from the evaluated sums.
+static __global__ void k_gnewton(Params P, GlobalRelaxState* gs, const double* __restrict__ elem_a,
+                          const double* __restrict__ elem_s, const double* __restrict__ A,
+                          const double* __restrict__ elem_r, const double* __restrict__ elem_dr,
+                          unsigned long long* gmin_bits, int* status, double delta_floor, double gamma_max,
+                          int phase) {
+  __shared__ double sh[256];
+  const int inst = blockIdx.x;
+  const InstGeom& G = geom_of(P, inst);
+  const int off = G.off, n = G.nx * G.ny * G.nz;
+  GlobalRelaxState& S = gs[inst];
+  if (phase == 0) {
+    const double a = block_sum(elem_a, off, n, sh);
+    const double ssum = block_sum(elem_s, off, n, sh);
+    const double At = block_sum(A, off, n, sh);
+    if (threadIdx.x == 0) {
+      S.a = a;
+      S.A = At;
+      S.lo = 0.0;
+      S.hi = gamma_max;
+      S.hi_known = 0;
+      S.done = 0;
+      S.result = __longlong_as_double(0x7ff0000000000000LL);
+      if (!(sqrt(2.0 * a / ssum) > delta_floor)) {
+        S.done = 1;
+      } else if (!(At < 0.0)) {
+        atomicOr(status, kStatusNoRoot);
+        S.done = 1;
+      } else {
+        S.g = fmin(fmax(-At / a, 1e-3), gamma_max);
+      }
+    }
+    return;
+  }
+  if (S.done) return;
+  const double R = block_sum(elem_r, off, n, sh);
+  const double DR = block_sum(elem_dr, off, n, sh);
+  if (threadIdx.x != 0) return;
+  const double gcur = S.g;
+  const bool phys = !isnan(R);
+  const double rv = R + gcur * S.A;
+  const double dv = DR + S.A;
+  if (!phys || rv > 0.0) {
+    S.hi = gcur;
+    S.hi_known = 1;
+  } else {
+    S.lo = gcur;
+  }
+  if (phys && rv == 0.0) {
+    S.result = gcur;
+    S.done = 1;
+  } else {
+    const double step = rv / dv;
+    const double newton = gcur - step;
+    const bool nok = phys && dv > 0.0 && isfinite(newton) && newton > S.lo && newton < S.hi;
+    if (phys && dv > 0.0 && fabs(step) <= 1e-8 * gcur) {
+      S.result = fmin(fmax(newton, S.lo), S.hi);
+      S.done = 1;
+    } else if (S.hi - S.lo <= 8.881784197001252e-16 * fmax(1.0, gcur)) {
+      S.result = S.lo;
+      S.done = 1;
+    } else {
+      S.g = nok ? newton : (S.hi_known ? 0.5 * (S.lo + S.hi) : fmin(2.0 * gcur, gamma_max));
+      if (!S.hi_known && S.lo >= gamma_max) {
+        S.result = gamma_max;
+        S.done = 1;
+      }
+    }
+  }
+  if (S.done) gmin_bits[inst] = (unsigned long long)__double_as_longlong(S.result);
+}
+
+// after the iterations: instances that did not converge take their last iterate;
+// every element reports its instance's gamma
+static __global__ void k_gfinish(Params P, GlobalRelaxState* gs, unsigned long long* gmin_bits, double* gamma_elem) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P.K; e += gridDim.x * blockDim.x) {
+    const int inst = inst_of(P, e);
+    const GlobalRelaxState& S = gs[inst];
+    const double g = S.done ? S.result : S.g;
+    gamma_elem[e] = g;
+    if (e == geom_of(P, inst).off) gmin_bits[inst] = (unsigned long long)__double_as_longlong(g);
   }
 }
 
@@ -675,6 +864,20 @@ void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* a
 template <int P1, typename TF>
 void Launcher<P1, TF>::relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid) {
   k_relax<P1><<<grid, 128, 0, st>>>(P, sr);
+}
+
+template <int P1, typename TF>
+void Launcher<P1, TF>::global_relax(const Params& P, const GlobalRelaxArgs& ga, cudaStream_t st, int grid,
+                                    int iterations) {
+  k_gsetup<P1><<<grid, 128, 0, st>>>(P, ga.u, ga.d, ga.nodes, ga.elem_a, ga.elem_s);
+  k_gnewton<<<P.ninst, 256, 0, st>>>(P, ga.gs, ga.elem_a, ga.elem_s, ga.A, ga.elem_r, ga.elem_dr, ga.gmin_bits,
+                                      ga.status, ga.delta_floor, ga.gamma_max, 0);
+  for (int it = 0; it < iterations; ++it) {
+    k_geval<P1><<<grid, 128, 0, st>>>(P, ga.nodes, ga.gs, ga.elem_r, ga.elem_dr);
+    k_gnewton<<<P.ninst, 256, 0, st>>>(P, ga.gs, ga.elem_a, ga.elem_s, ga.A, ga.elem_r, ga.elem_dr, ga.gmin_bits,
+                                        ga.status, ga.delta_floor, ga.gamma_max, 1);
+  }
+  k_gfinish<<<(P.K + 255) / 256, 256, 0, st>>>(P, ga.gs, ga.gmin_bits, ga.gamma_elem);
 }
 
 template <int P1, typename TF>

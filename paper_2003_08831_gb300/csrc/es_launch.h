@@ -57,6 +57,29 @@ struct StageRelax {
   double gamma_max;
 };
 
+// global relaxation: per-instance Newton state
+struct GlobalRelaxState {
+  double g, lo, hi, a, A, result;
+  int hi_known, done;
+};
+
+struct GlobalRelaxArgs {
+  const double* u;
+  const double* d;
+  const double* A;       // per element
+  double* nodes;         // [4][N] scratch
+  double* elem_a;        // [K]
+  double* elem_s;        // [K]
+  double* elem_r;        // [K]
+  double* elem_dr;       // [K]
+  GlobalRelaxState* gs;  // [ninst]
+  unsigned long long* gmin_bits;
+  double* gamma_elem;
+  int* status;
+  double delta_floor, gamma_max;
+};
+
+constexpr int kGlobalRelaxIterations = 8;
 constexpr int kVolumeVariants = 3;
 
 template <int P1, typename TF>
@@ -70,6 +93,7 @@ struct Launcher {
                      cudaStream_t st, int variant);
   static void relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid);
   static void entropy(const Params& P, const double* q, double* eta, cudaStream_t st, int grid);
+  static void global_relax(const Params& P, const GlobalRelaxArgs& ga, cudaStream_t st, int grid, int iterations);
 };
 
 // per-instance step bookkeeping: gamma = min gamma_kappa (or 1), t += gamma dt,

@@ -152,9 +152,9 @@ def compare_advance(mesh, U, lo, hi, phys, tabname, nsteps, mode="local", cfl=0.
     dt = rk.stable_dt(mesh, U, phys, cfl)
     Uo, to, hist = rk.advance(mesh, U, dt, nsteps, phys, rk.TABLEAUX[tabname], mode=mode)
     sens_g, sens_gk = gamma_sensitivity(mesh, U, dt, nsteps, phys, rk.TABLEAUX[tabname], mode, hist)
+    relax_mode = {"local": B.ES_RELAX_LOCAL, "global": B.ES_RELAX_GLOBAL, "none": B.ES_RELAX_NONE}[mode]
     s = solver(mesh.p, mesh.n, lo, hi, mu=phys.mu, Pr=phys.Pr, interface_diss=phys.diss,
-               rk=B.ES_RK_BS3 if tabname == "BS3" else B.ES_RK_RK4,
-               relax=B.ES_RELAX_LOCAL if mode == "local" else B.ES_RELAX_NONE, **kw)
+               rk=B.ES_RK_BS3 if tabname == "BS3" else B.ES_RK_RK4, relax=relax_mode, **kw)
     q = s.to_device(U)
     t, gh, gk = s.advance(q, nsteps, dt)
     assert s.status() == 0
@@ -190,6 +190,13 @@ def test_advance_rk4_ec_ragged():
 def test_advance_navier_stokes():
     mesh, U, lo, hi = vortex_setup(N=3, p=4, nz=2)
     compare_advance(mesh, U, lo, hi, dg.Physics(G, mu=0.005, Pr=0.72, diss=1), "BS3", 5)
+
+
+def test_advance_global_relaxation():
+    """Global relaxation (one gamma for eta = sum eta_kappa), the paper's comparison mode."""
+    mesh, U, lo, hi = vortex_setup(N=4, p=3, nz=2)
+    g = compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=1), "BS3", 6, mode="global")
+    assert np.all(np.abs(g - 1) < 0.05)
 
 
 def test_advance_baseline_no_relaxation():
@@ -445,3 +452,20 @@ def test_local_gamma_variation_x6():
     assert g.size > 0
     assert np.max(np.abs(g - 1.0)) < gold["bound"], np.max(np.abs(g - 1.0))
     s.close()
+
+
+def test_reciprocal_matches_ieee_division():
+    """The kernels' FP64 reciprocal (hardware approximation + two Newton steps) against
+    IEEE 1/x over random mantissas and exponents 2^-300 .. 2^300: within one ulp."""
+    import torch
+    from paper_2003_08831_gb300 import _binding as B
+    rng = np.random.default_rng(7)
+    x = np.ldexp(rng.uniform(1.0, 2.0, 1 << 20), rng.integers(-300, 300, 1 << 20))
+    x[::2] *= -1.0
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    B.es_reciprocal(xd, out)
+    torch.cuda.synchronize()
+    ref = 1.0 / x
+    ulp = np.abs(out.cpu().numpy().view(np.int64) - ref.view(np.int64))
+    assert ulp.max() <= 1, ulp.max()
