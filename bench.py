@@ -17,6 +17,7 @@ problems, no data-path collective: weak scaling); rank 0 prints one JSON line.
 the same workload (rank 0 only).
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -62,6 +63,20 @@ def volume_flops_per_element(p, ns=False, with_A=False):
     if ns:
         f += lines * 4 * (2 * P1 * P1 + 8) + lines * 4 * P1
     return f
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_volume launch of the
+# default workload, from the ncu capture summarised in profiles/ (stage 3 of a step, FP64).
+# It is reported only while the kernel sources hash to the value the capture was taken with.
+VOLUME_TRAFFIC = {"source_sha1": None, "bytes_per_launch": None}
+
+
+def kernel_source_sha1():
+    h = hashlib.sha1()
+    for f in ("es_kernels.cuh", "es_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2003_08831_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def fp_peak_tflops(precision, sm_mhz):
@@ -129,6 +144,25 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------
+def aggregate(ms_local, units_local, dist=None, device="cpu"):
+    """Weak-scaling aggregation over ranks: the slowest rank's time and the units of
+    work of all ranks (no data-path collective; this runs once after the timed
+    region).  Returns (max ms, total units)."""
+    if dist is None:
+        return float(ms_local), float(units_local)
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def shard(count, rank, world):
+    """Indices of `count` independent instances owned by `rank` (round robin)."""
+    return list(range(rank, count, world))
+
+
 def initial_state(solver, wl, gamma_gas=1.4):
     from paper_2003_08831_gb300 import inputs
     xyz = solver.coords()
@@ -366,14 +400,10 @@ def run_full(args, rank, world, local_rank):
     __graft_entry__.build()
     wl = WORKLOADS[args.workload]
     res = measure_device(wl, args.steps, args.warmup, dist=dist, clocks_gpu=local_rank)
-    ms = res["ms"]
-    if dist is not None:
-        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms, units = aggregate(res["ms"], res["nodes"] * STAGES * args.steps, dist, "cuda")
     clocks = res.pop("clocks", None)
     nodes = res["nodes"]
-    value = world * nodes * STAGES * args.steps / (ms / 1e3)
+    value = units / (ms / 1e3)
     if args.quick:
         res["solver"].close()
         if rank == 0:
@@ -413,7 +443,10 @@ def run_full(args, rank, world, local_rank):
         "gpu_launches": int(res["launches"]),
         "roofline": {"bound": "alu", "kernel": "k_volume (flux differencing + SATs)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None,
+                     "traffic": (VOLUME_TRAFFIC["bytes_per_launch"]
+                                 if VOLUME_TRAFFIC["source_sha1"] == kernel_source_sha1() and wl is WORKLOADS[MAIN]
+                                 else None),
+                     "traffic_unit": "bytes per launch (ncu, same kernel sources)",
                      "peak_source": "%s ALU peak from unit counts x median SM clock (%.0f MHz): 152 SMs x %s"
                                     % ("FP64" if wl["precision"] == 0 else "FP32", sm_mhz,
                                        "2 DFMA/clk" if wl["precision"] == 0 else "128 FFMA/clk"),

@@ -4,9 +4,40 @@ Argument marshalling and bookkeeping only; all arithmetic of the scheme runs in
 libes.so.  ``stable_dt`` is the harness' time-step rule (computed once from the
 initial state, then fixed).
 """
+import json
+
 import numpy as np
 
 from . import _binding as B
+
+CHECKPOINT_MAGIC = "es-relax-checkpoint-v1"
+
+
+def save_checkpoint(path, q, meta):
+    """Raw little-endian FP64 state [5][K][Np] followed by nothing else, plus a JSON
+    header file path + '.json' holding meta (config, t, step, dt, ...).  The step is
+    deterministic (fixed reduction orders, order-free min), so resuming from a
+    checkpoint reproduces an uninterrupted run bit for bit."""
+    q = np.ascontiguousarray(np.asarray(q, dtype="<f8"))
+    header = dict(meta)
+    header["magic"] = CHECKPOINT_MAGIC
+    header["shape"] = list(q.shape)
+    with open(path, "wb") as f:
+        f.write(q.tobytes())
+    with open(path + ".json", "w") as f:
+        json.dump(header, f, indent=1, sort_keys=True)
+
+
+def load_checkpoint(path):
+    with open(path + ".json") as f:
+        header = json.load(f)
+    if header.get("magic") != CHECKPOINT_MAGIC:
+        raise ValueError("not a checkpoint: %s" % path)
+    q = np.fromfile(path, dtype="<f8")
+    shape = tuple(header["shape"])
+    if q.size != int(np.prod(shape)):
+        raise ValueError("checkpoint %s is truncated" % path)
+    return q.reshape(shape).astype(np.float64), header
 
 
 class Solver:
@@ -88,6 +119,26 @@ class Solver:
 
     def launch_count(self):
         return B.es_launch_count(self.ctx)
+
+    def config_dict(self):
+        c = self.cfg
+        return {"p": c.p, "n": [c.nx, c.ny, c.nz], "lo": list(c.lo), "hi": list(c.hi), "gamma_gas": c.gamma_gas,
+                "mu": c.mu, "Pr": c.Pr, "R": c.R, "interface_diss": c.interface_diss, "relax": c.relax,
+                "rk": c.rk, "precision": c.precision, "delta_floor": c.delta_floor}
+
+    def checkpoint(self, path, q, t, step, dt):
+        """Write the device state q, time t (float) and step counter to path (see save_checkpoint)."""
+        save_checkpoint(path, q.detach().cpu().numpy(),
+                        {"config": self.config_dict(), "t": float(t), "step": int(step), "dt": float(dt)})
+
+    @classmethod
+    def resume(cls, path, device="cuda"):
+        """(solver, q on the device, t, step, dt) from a checkpoint."""
+        q, h = load_checkpoint(path)
+        c = h["config"]
+        s = cls(c["p"], tuple(c["n"]), tuple(c["lo"]), tuple(c["hi"]), c["gamma_gas"], c["mu"], c["Pr"], c["R"],
+                c["interface_diss"], c["relax"], c["rk"], c["precision"], c["delta_floor"], device=device)
+        return s, s.to_device(q), h["t"], h["step"], h["dt"]
 
     def autotune(self, q, stream=None):
         B.es_autotune(self.ctx, q, stream)
