@@ -1,0 +1,52 @@
+"""Section 4.1.1 on the GPU path: design-order convergence of the locally relaxed
+scheme on the isentropic vortex (closed form, Eq. (vortex-solution)), compared at
+the relaxed time t_gamma, at resolutions the CPU oracle cannot reach quickly.
+
+The paper pairs p = 2 with BSRK(4,3) and p = 3 with RK(4,4) (Table 1); the
+observed L2 density rates there are 3.2 and 4.5.  Here: entropy-stable (Rusanov)
+interfaces, a 2D vortex extruded over one element in x3, periodic box
+[-5, 5]^2, t_end = 1, CFL 0.5 (the time step shrinks with h).
+"""
+import numpy as np
+import pytest
+
+from paper_2003_08831_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def l2_density_error(p, N, rk):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2003_08831_gb300.solver import Solver, stable_dt
+    lo, hi = (-5.0, -5.0, 0.0), (5.0, 5.0, 10.0 / N)
+    s = Solver(p, (N, N, 1), lo, hi, rk=rk)
+    xyz = s.coords()
+    q0 = inputs.vortex_state(xyz[0], xyz[1], 0.0, period=10.0)
+    h = 10.0 / N
+    dt = stable_dt(q0, p, [h, h, h], 0.5)
+    nsteps = int(np.ceil(1.0 / dt))
+    q = s.to_device(q0)
+    t, gh, _ = s.advance(q, nsteps, dt)
+    assert s.status() == 0
+    exact = inputs.vortex_state(xyz[0], xyz[1], t.item(), period=10.0)
+    from oracle import sbp
+    _, w, _ = sbp.sbp_operator(p)
+    W = (w[:, None, None] * w[None, :, None] * w[None, None, :]).reshape(-1) * (h / 2) ** 3
+    err = q.cpu().numpy()[0] - exact[0]
+    l2 = np.sqrt(np.sum(W[None, :] * err * err) / (100.0 * h))
+    s.close()
+    return l2, gh.cpu().numpy()
+
+
+@pytest.mark.parametrize("p,rk,rate_min", [(2, 0, 2.7), (3, 1, 3.7)])
+def test_vortex_design_order(p, rk, rate_min):
+    errs = []
+    for N in (8, 16, 32):
+        e, g = l2_density_error(p, N, rk)
+        assert np.all(np.abs(g - 1.0) < 0.05)
+        errs.append(e)
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] > rate_min, (errs, rates)
