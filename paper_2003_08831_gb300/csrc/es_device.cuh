@@ -284,11 +284,58 @@ __device__ __forceinline__ bool relax_node_eval(const RelaxNode& nd, double g, d
   return true;
 }
 
+// Taylor coefficients in g of D_n(g)/rho_n up to g^kSeries for one node (index k
+// of Dk; Dk[0] = Dk[1] = 0).  With x = g X0, q = 1/(1 + g X0) = sum (-X0)^k g^k,
+// K = g^2 V2 q/2, y = g Y0 - (gam-1) K and L = log1p(y) from (1+y) L' = y':
+//   L_n = y_n - (1/n) sum_{j=1}^{n-1} (n-j) y_j L_{n-j},
+//   phi_k = (-1)^k X0^k/(k(k-1)),  psi_k = y_k - L_k,  (x log1p y)_k = X0 L_{k-1},
+//   D_k = [gam phi_k + psi_k - X0 L_{k-1}]/(gam-1) + K_k.
+// The leading coefficient is D_2 = [(gam-1) X0^2 + (X0 - Y0)^2]/(2(gam-1)) + V2/2.
+// Used where every |X0|, |Y0|, sqrt(V2) of the element is below 1e-4: then up to
+// g = 8 each further order is smaller by < 1e-3 and the truncation after g^8 is
+// below 1e-20 of the leading term.
+constexpr int kSeries = 8;
+__device__ __forceinline__ void relax_node_series(const RelaxNode& nd, double gam, double inv_gm1,
+                                                  double Dk[kSeries + 1]) {
+  double y[kSeries + 1], L[kSeries + 1], K[kSeries + 1];
+  const double mX = -nd.X0;
+  double pw = 1.0;  // (-X0)^(k-2)
+  K[0] = K[1] = 0.0;
+  for (int k = 2; k <= kSeries; ++k) {
+    K[k] = 0.5 * nd.V2 * pw;
+    pw *= mX;
+  }
+  y[0] = 0.0;
+  y[1] = nd.Y0;
+  for (int k = 2; k <= kSeries; ++k) y[k] = -(gam - 1.0) * K[k];
+  L[0] = 0.0;
+  for (int n = 1; n <= kSeries; ++n) {
+    double s = 0.0;
+    for (int j = 1; j < n; ++j) s = fma(double(n - j) * y[j], L[n - j], s);
+    L[n] = y[n] - s / double(n);
+  }
+  double xk = nd.X0 * nd.X0;  // X0^k, k = 2
+  double sgn = 1.0;           // (-1)^k
+  Dk[0] = Dk[1] = 0.0;
+  for (int k = 2; k <= kSeries; ++k) {
+    const double phi = sgn * xk / double(k * (k - 1));
+    Dk[k] = (gam * phi + (y[k] - L[k]) - nd.X0 * L[k - 1]) * inv_gm1 + K[k];
+    xk *= nd.X0;
+    sgn = -sgn;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // warp reductions (butterfly: every lane ends with the same sum/min)
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 

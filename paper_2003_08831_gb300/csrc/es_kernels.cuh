@@ -510,7 +510,68 @@ __global__ void k_relax(Params P, StageRelax sr) {
     else A = sr.A[e];
     double gk = __longlong_as_double(0x7ff0000000000000LL);  // +inf: unconstrained
     const double delta = sqrt(2.0 * a / ssum);
-    if (delta > sr.delta_floor) {
+    double mx = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) mx = fmax(mx, fmax(fmax(fabs(nd[r].X0), fabs(nd[r].Y0)), sqrt(nd[r].V2)));
+    const bool series = warp_max(mx) <= 1e-4;
+    if (delta > sr.delta_floor && A < 0.0 && series) {
+      // small changes: r(g) = sum_k C_k g^k + A g from per-node Taylor coefficients,
+      // then Newton on the polynomial (scalar, every lane identical)
+      double C[kSeries + 1];
+#pragma unroll
+      for (int k = 0; k <= kSeries; ++k) C[k] = 0.0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (nd[r].c != 0.0) {
+          double Dk[kSeries + 1];
+          relax_node_series(nd[r], gam, inv_gm1, Dk);
+#pragma unroll
+          for (int k = 2; k <= kSeries; ++k) C[k] = fma(nd[r].c, Dk[k], C[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 2; k <= kSeries; ++k) C[k] = warp_sum(C[k]);
+      double lo = 0.0, hi = sr.gamma_max;
+      bool hi_known = false;
+      double gcur = fmin(fmax(-A / a, 1e-3), sr.gamma_max);
+      for (int it = 0; it < 200; ++it) {
+        double rv = C[kSeries], dv = kSeries * C[kSeries];
+        for (int k = kSeries - 1; k >= 2; --k) {
+          rv = fma(rv, gcur, C[k]);
+          dv = fma(dv, gcur, k * C[k]);
+        }
+        rv = (rv * gcur + A) * gcur;  // sum_{k>=2} C_k g^k + A g
+        dv = dv * gcur + A;
+        if (rv > 0.0) {
+          hi = gcur;
+          hi_known = true;
+        } else {
+          lo = gcur;
+        }
+        const double step = rv / dv;
+        const double newton = gcur - step;
+        if (dv > 0.0 && fabs(step) <= 8.881784197001252e-16 * fmax(1.0, gcur)) {
+          gk = fmin(fmax(newton, lo), hi);
+          break;
+        }
+        if (rv == 0.0) {
+          gk = gcur;
+          break;
+        }
+        if (hi - lo <= 8.881784197001252e-16 * fmax(1.0, gcur)) {
+          gk = lo;
+          break;
+        }
+        const bool nok = dv > 0.0 && isfinite(newton) && newton > lo && newton < hi;
+        if (nok) gcur = newton;
+        else if (!hi_known) gcur = (gcur >= sr.gamma_max) ? sr.gamma_max : fmin(2.0 * gcur, sr.gamma_max);
+        else gcur = 0.5 * (lo + hi);
+        if (!hi_known && lo >= sr.gamma_max) {
+          gk = sr.gamma_max;
+          break;
+        }
+      }
+    } else if (delta > sr.delta_floor) {
       if (!(A < 0.0)) {
         if (lane == 0) atomicOr(sr.status, kStatusNoRoot);
       } else {
