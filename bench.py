@@ -40,11 +40,18 @@ WORKLOADS = {
     # the metric's configuration: Euler TGV 32^3 p=3 FP64, 200 steps
     "tgv_euler_p3_32^3_fp64": dict(p=3, n=32, mu=0.0, precision=0, ic="tgv", steps=200),
     "tgv_euler_p3_32^3_mixed": dict(p=3, n=32, mu=0.0, precision=1, ic="tgv", steps=200),
+    "tgv_euler_p3_32^3_fp64x": dict(p=3, n=32, mu=0.0, precision=2, ic="tgv", steps=200),
+    "tgv_ns_re1600_p4_32^3_fp64x": dict(p=4, n=32, mu=1.0 / 1600.0, precision=2, ic="tgv", steps=200),
     "tgv_ns_re1600_p4_32^3_fp64": dict(p=4, n=32, mu=1.0 / 1600.0, precision=0, ic="tgv", steps=200),
     "tgv_ns_re1600_p4_32^3_mixed_noise": dict(p=4, n=32, mu=1.0 / 1600.0, precision=1, ic="tgv_noise", steps=200),
     "vortex_euler_p3_4^3_fp64": dict(p=3, n=4, mu=0.0, precision=0, ic="vortex", steps=20),
 }
 MAIN = "tgv_euler_p3_32^3_fp64"
+PRECISION_LABEL = {0: "FP64",
+                   1: "mixed (FP32 fluxes, FP64 state/estimate/gamma)",
+                   2: "FP64X (float-float fluxes/SATs/viscous terms on the FP32 pipe, ~2^-47 per operation; "
+                      "FP64 state/estimate/gamma)"}
+DTYPE = {0: "f64", 1: "f64+f32", 2: "f64+f32x2"}
 STAGES = 3  # BS3: b_4 = 0
 
 
@@ -152,7 +159,7 @@ def workload_config(name):
     return {"workload": name, "elements": K, "p": wl["p"], "nodes": K * P1 ** 3, "rk": "BS3 (3 stages)",
             "relaxation": "local", "cfl": 0.5, "interface": "EC + Rusanov",
             "physics": "Navier-Stokes Re 1600 Pr 0.72" if wl["mu"] > 0 else "Euler",
-            "precision": "FP64" if wl["precision"] == 0 else "mixed (FP32 fluxes, FP64 state/estimate/gamma)",
+            "precision": PRECISION_LABEL[wl["precision"]],
             "l2": "inputs larger than L2 (state + 3 stage buffers + aux > 500 MB), no flush"}
 
 
@@ -448,7 +455,7 @@ def run_full(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["precision"] == 0 else "f64+f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[wl["precision"]],
         "data": "synthetic (closed-form Taylor-Green vortex, Mach 0.1)",
         "config": workload_config(args.workload),
         "dt": res["dt"], "gamma_range": [res["gamma_min"], res["gamma_max"]],
@@ -474,7 +481,8 @@ def run_full(args, rank, world, local_rank):
     out["e2e"] = measure_e2e(wl, min(args.steps, 20), 3)
     if world == 1 and not args.no_forms:
         forms = {}
-        for name in ["tgv_euler_p3_32^3_mixed", "tgv_ns_re1600_p4_32^3_fp64", "tgv_ns_re1600_p4_32^3_mixed_noise"]:
+        for name in ["tgv_euler_p3_32^3_mixed", "tgv_euler_p3_32^3_fp64x", "tgv_ns_re1600_p4_32^3_fp64",
+                     "tgv_ns_re1600_p4_32^3_fp64x", "tgv_ns_re1600_p4_32^3_mixed_noise"]:
             w2 = WORKLOADS[name]
             steps2 = 50
             r2 = measure_device(w2, steps2, 3)
@@ -487,11 +495,14 @@ def run_full(args, rank, world, local_rank):
                            "kernel_share": {k: round(v[0] / t2, 4) for k, v in p2.items() if v[1] > 0},
                            "speedup_vs_fp64_same_physics": None}
             del r2
-        for prec, name in [(0, "batched_vortex_256_fp64"), (1, "batched_vortex_256_mixed")]:
+        for prec, name in [(0, "batched_vortex_256_fp64"), (1, "batched_vortex_256_mixed"),
+                           (2, "batched_vortex_256_fp64x")]:
             forms[name] = measure_batch(prec, 20, 3)
-        fp = {"tgv_euler_p3_32^3_mixed": value,
+        fp = {"tgv_euler_p3_32^3_mixed": value, "tgv_euler_p3_32^3_fp64x": value,
+              "tgv_ns_re1600_p4_32^3_fp64x": forms["tgv_ns_re1600_p4_32^3_fp64"]["value"],
               "tgv_ns_re1600_p4_32^3_mixed_noise": forms["tgv_ns_re1600_p4_32^3_fp64"]["value"],
-              "batched_vortex_256_mixed": forms["batched_vortex_256_fp64"]["value"]}
+              "batched_vortex_256_mixed": forms["batched_vortex_256_fp64"]["value"],
+              "batched_vortex_256_fp64x": forms["batched_vortex_256_fp64"]["value"]}
         for k, base in fp.items():
             forms[k]["speedup_vs_fp64_same_physics"] = forms[k]["value"] / base
         for k in forms:

@@ -46,6 +46,10 @@ extern "C" {
 
 #define ES_FP64 0  /* every operation in FP64 */
 #define ES_MIXED 1 /* FP32 fluxes/SATs/viscous terms; FP64 state, entropy sums, gamma solve */
+#define ES_FP64X 2 /* fluxes/SATs/viscous terms in float-float arithmetic on the FP32 pipe
+                      (hi + lo pairs of floats, ~2^-47 relative per operation, FP32 exponent
+                      range); FP64 state, entropy sums and gamma solve.  es_rhs_noalloc
+                      evaluates such a configuration with the FP64 kernels. */
 
 #define ES_RELAX_NONE 0  /* baseline RK, gamma = 1 */
 #define ES_RELAX_LOCAL 1 /* gamma = min_kappa gamma_kappa (Theorem 2.3) */
@@ -65,11 +69,11 @@ typedef struct {
   int interface_diss;   /* 0: entropy-conservative SAT^I; 1: + Rusanov diss^I */
   int relax;            /* ES_RELAX_* */
   int rk;               /* ES_RK_* */
-  int precision;        /* ES_FP64 or ES_MIXED */
+  int precision;        /* ES_FP64, ES_MIXED or ES_FP64X */
   double delta_floor;   /* elements whose RMS relative change over the step is
                            <= delta_floor are unconstrained (gamma_kappa = +inf);
-                           <= 0 selects 1e-8 (ES_FP64) or 4e-6 (ES_MIXED: 64 eps_32,
-                           above the FP32 right-hand side's rounding noise) */
+                           <= 0 selects 1e-8 (ES_FP64, ES_FP64X) or 4e-6 (ES_MIXED:
+                           64 eps_32, above the FP32 right-hand side's rounding noise) */
 } es_config;
 
 /* Mesh, LGL/SBP tables (Section 3.1: diagonal-norm SBP on LGL nodes) and

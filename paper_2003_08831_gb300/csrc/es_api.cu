@@ -116,7 +116,7 @@ int validate_config(const es_config& C) {
   if (C.p < 2 || C.p > 5 || C.nx < 1 || C.ny < 1 || C.nz < 1) return ES_ERR_INVALID;
   if (!(C.gamma_gas > 1.0) || !(C.R > 0.0) || C.mu < 0.0 || (C.mu > 0.0 && !(C.Pr > 0.0))) return ES_ERR_INVALID;
   if (C.rk != ES_RK_BS3 && C.rk != ES_RK_RK4) return ES_ERR_INVALID;
-  if (C.precision != ES_FP64 && C.precision != ES_MIXED) return ES_ERR_INVALID;
+  if (C.precision != ES_FP64 && C.precision != ES_MIXED && C.precision != ES_FP64X) return ES_ERR_INVALID;
   if (C.relax != ES_RELAX_NONE && C.relax != ES_RELAX_LOCAL && C.relax != ES_RELAX_GLOBAL) return ES_ERR_INVALID;
   if (C.interface_diss != 0 && C.interface_diss != 1) return ES_ERR_INVALID;
   for (int m = 0; m < 3; ++m)
@@ -157,6 +157,11 @@ void build_params(const es_config& C, Params* out) {
     for (int j = 0; j < P1; ++j) {
       P.D[i * P1 + j] = D[i * P1 + j];
       P.D2[i * P1 + j] = (i == j) ? 0.0 : 2.0 * D[i * P1 + j];
+      const ff d1(P.D[i * P1 + j]), d2(P.D2[i * P1 + j]);
+      P.Dff[0][i * P1 + j] = d1.hi;
+      P.Dff[1][i * P1 + j] = d1.lo;
+      P.D2ff[0][i * P1 + j] = d2.hi;
+      P.D2ff[1][i * P1 + j] = d2.lo;
     }
   }
   P.inv_omega_end = 1.0 / w[0];
@@ -191,7 +196,8 @@ struct Group {
   es_config cfg;  // physics (and, for a context, the mesh)
   int P1 = 0, Np = 0, K = 0, ninst = 0;
   long long N = 0;
-  size_t tf = 8;  // bytes per flux value (8 FP64, 4 mixed)
+  size_t tf = 8;  // bytes per flux value (8 FP64 and float-float, 4 mixed)
+  bool ffx = false;  // float-float flux arithmetic (ES_FP64X)
   Params P;
   int vol_variant = 0;
   std::vector<InstGeom> geom;      // host copy of the instance table
@@ -282,10 +288,10 @@ int dev_alloc_bytes(void** p, size_t bytes) {
 template <typename F>
 int dispatch(const Group& g, F&& f) {
   switch (g.P1) {
-    case 3: return g.tf == 8 ? f(Launcher<3, double>()) : f(Launcher<3, float>());
-    case 4: return g.tf == 8 ? f(Launcher<4, double>()) : f(Launcher<4, float>());
-    case 5: return g.tf == 8 ? f(Launcher<5, double>()) : f(Launcher<5, float>());
-    case 6: return g.tf == 8 ? f(Launcher<6, double>()) : f(Launcher<6, float>());
+    case 3: return g.tf == 4 ? f(Launcher<3, float>()) : g.ffx ? f(Launcher<3, ff>()) : f(Launcher<3, double>());
+    case 4: return g.tf == 4 ? f(Launcher<4, float>()) : g.ffx ? f(Launcher<4, ff>()) : f(Launcher<4, double>());
+    case 5: return g.tf == 4 ? f(Launcher<5, float>()) : g.ffx ? f(Launcher<5, ff>()) : f(Launcher<5, double>());
+    case 6: return g.tf == 4 ? f(Launcher<6, float>()) : g.ffx ? f(Launcher<6, ff>()) : f(Launcher<6, double>());
   }
   return ES_ERR_INVALID;
 }
@@ -387,7 +393,8 @@ int group_init(Group& g, const es_config* insts, int n, int stages, bool own_sta
   g.P1 = C.p + 1;
   g.Np = g.P1 * g.P1 * g.P1;
   g.ninst = n;
-  g.tf = C.precision == ES_MIXED ? 4 : 8;
+  g.tf = C.precision == ES_MIXED ? 4 : 8;  // bytes per flux-precision value (float-float: 8)
+  g.ffx = C.precision == ES_FP64X;
   build_params(C, &g.P);
   long long K = 0;
   g.geom.resize(n);

@@ -10,6 +10,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "es_ff.cuh"
+
 namespace es {
 
 constexpr int kMaxP1 = 6;
@@ -29,6 +31,8 @@ struct InstGeom {
 struct Params {
   double D[kMaxP1 * kMaxP1];   // SBP derivative on [-1, 1], row-major
   double D2[kMaxP1 * kMaxP1];  // 2 D_ij (i != j), 0 on the diagonal
+  float Dff[2][kMaxP1 * kMaxP1];   // D and 2 D split into float-float (hi, lo)
+  float D2ff[2][kMaxP1 * kMaxP1];
   double omega[kMaxP1];        // LGL weights
   double inv_omega_end;        // 1/omega_0 = 1/omega_p
   double gam;                  // ratio of specific heats
@@ -73,6 +77,27 @@ __device__ __forceinline__ double mass_weight(const Params& P, double J, int n) 
   return J * P.omega[i] * P.omega[j] * P.omega[k];
 }
 
+// operator entries in the flux precision T (float-float: the split tables)
+template <typename T> struct Tab;
+template <> struct Tab<double> {
+  static __device__ __forceinline__ double D(const Params& P, int i) { return P.D[i]; }
+  static __device__ __forceinline__ double D2(const Params& P, int i) { return P.D2[i]; }
+};
+template <> struct Tab<float> {
+  static __device__ __forceinline__ float D(const Params& P, int i) { return float(P.D[i]); }
+  static __device__ __forceinline__ float D2(const Params& P, int i) { return float(P.D2[i]); }
+};
+template <> struct Tab<ff> {
+  static __device__ __forceinline__ ff D(const Params& P, int i) { return ff(P.Dff[0][i], P.Dff[1][i]); }
+  static __device__ __forceinline__ ff D2(const Params& P, int i) { return ff(P.D2ff[0][i], P.D2ff[1][i]); }
+};
+
+// acc += a b in the flux precision (the float-float form keeps the product and
+// sum errors, see es_ff.cuh; FP64/FP32 use one fma, as contraction would)
+__device__ __forceinline__ void fma_acc(double& acc, double a, double b) { acc = fma(a, b, acc); }
+__device__ __forceinline__ void fma_acc(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
+__device__ __forceinline__ void fma_acc(ff& acc, ff a, ff b) { ff_fma_acc(acc, a, b); }
+
 // ---------------------------------------------------------------------------
 // Parameter-vector state used by the two-point flux: z = sqrt(rho/p) (1, v, p).
 constexpr int kAux = 5;       // planes read by the volume kernel
@@ -105,6 +130,7 @@ __device__ __forceinline__ double fast_rcp(double x) {
   return fma(r, e, r);
 }
 __device__ __forceinline__ float fast_rcp(float x) { return 1.0f / x; }
+__device__ __forceinline__ ff fast_rcp(ff x) { return ff_rcp(x); }
 
 // |z| <= t for a positive threshold t, on the integer pipe (sign bit cleared)
 __device__ __forceinline__ bool abs_le(double z, double t) {
@@ -176,6 +202,88 @@ __device__ __forceinline__ void ec_flux(const Zstate<T>& a, const Zstate<T>& b, 
   f[3] = mass * uz;
   f[1 + m] += p1;
   f[4] = um * p2g + (T(0.5) * mass) * q2;
+}
+
+// The same flux in float-float arithmetic (precision mode ES_FP64X).  The
+// series branch keeps the leading u/3 (u/12) terms in float-float and the
+// higher-order terms, below 2.1e-5 relative to them for u < 1e-4, in FP32; the
+// sums and differences of the z's whose high parts agree within a factor two
+// are exact in their high part (Sterbenz), so D = (a.hi - b.hi) + (a.lo - b.lo)
+// carries a single rounding.  The rare logarithmic branch (u >= 1e-4) is taken
+// in FP64.
+__device__ __forceinline__ ff ff_series_f(ff u) {
+  // F(u) = 1 + u/3 + u^2/5 + u^3/7
+  constexpr float th = float(1.0 / 3.0);
+  constexpr float tl = float(1.0 / 3.0 - double(th));
+  const float p = __fmul_rn(u.hi, th);
+  float e = __fmaf_rn(u.hi, th, -p);
+  e = __fmaf_rn(u.hi, tl, e);
+  e = __fmaf_rn(u.lo, th, e);
+  const float q = __fmul_rn(u.hi, __fmaf_rn(u.hi, 1.0f / 7.0f, 0.2f));  // u/5 + u^2/7
+  e = __fmaf_rn(u.hi, q, e);
+  const ff s = fast_two_sum(1.0f, p);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, e));
+}
+__device__ __forceinline__ ff ff_series_g(ff u) {
+  // (1/F(u))/4 = 1/4 - u/12 - u^2/45 - 11 u^3/945
+  constexpr float th = float(1.0 / 12.0);
+  constexpr float tl = float(1.0 / 12.0 - double(th));
+  const float p = __fmul_rn(u.hi, th);
+  float e = __fmaf_rn(u.hi, th, -p);
+  e = __fmaf_rn(u.hi, tl, e);
+  e = __fmaf_rn(u.lo, th, e);
+  const float q = __fmul_rn(u.hi, __fmaf_rn(u.hi, 11.0f / 945.0f, 1.0f / 45.0f));
+  e = __fmaf_rn(u.hi, q, e);
+  const ff s = fast_two_sum(0.25f, -p);
+  return fast_two_sum(s.hi, __fsub_rn(s.lo, e));
+}
+__device__ __forceinline__ ff ff_exact_diff(ff a, ff b) {
+  return ff_norm(ff(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ void ec_flux(const Zstate<ff>& a, const Zstate<ff>& b, int m, const FluxConst<ff>& C,
+                                        ff f[5]) {
+  const ff S1 = a.z[0] + b.z[0];
+  const ff S5 = a.z[4] + b.z[4];
+  const ff P15 = S1 * S5;
+  const ff inv = ff_rcp(P15);
+  const ff inv1 = S5 * inv;  // 1/S1
+  const ff is5 = S1 * inv;   // 1/S5
+  // high parts within a factor two: D exact up to the lo difference (else the
+  // FP64 branch below recomputes the mean and u is only used for the test)
+  const ff r1 = ff_exact_diff(a.z[0], b.z[0]) * inv1;
+  const ff r5 = ff_exact_diff(a.z[4], b.z[4]) * is5;
+  const ff u1 = r1 * r1, u5 = r5 * r5;
+  ff f1, g5;
+  if (u1.hi < 1e-4f) {
+    f1 = ff_series_f(u1);
+  } else {
+    const double A = double(a.z[0]), B = double(b.z[0]);
+    f1 = ff(0.5 * (A + B) * ::log(A / B) / (A - B));
+  }
+  if (u5.hi < 1e-4f) {
+    g5 = ff_series_g(u5);
+  } else {
+    const double A = double(a.z[4]), B = double(b.z[4]);
+    g5 = ff(0.5 * (A - B) / ((A + B) * ::log(A / B)));
+  }
+  const ff rho_hat = P15 * g5;
+  const ff u0 = (a.z[1] + b.z[1]) * inv1;
+  const ff uy = (a.z[2] + b.z[2]) * inv1;
+  const ff uz = (a.z[3] + b.z[3]) * inv1;
+  const ff p1 = S5 * inv1;
+  const ff p2g = p1 * (C.C1x * (g5 * f1) + C.C2x);
+  const ff um = m == 0 ? u0 : (m == 1 ? uy : uz);
+  const ff mass = rho_hat * um;
+  const ff q2 = u0 * u0 + uy * uy + uz * uz;
+  f[0] = mass;
+  f[1] = mass * u0;
+  f[2] = mass * uy;
+  f[3] = mass * uz;
+  // constant indices keep f in registers (m is a run-time value)
+  if (m == 0) f[1] += p1;
+  else if (m == 1) f[2] += p1;
+  else f[3] += p1;
+  f[4] = um * p2g + ff(0.5f * mass.hi, 0.5f * mass.lo) * q2;
 }
 
 // Conserved state from the parameter vector and iz1 = 1/z1 = sqrt(p/rho):
@@ -282,47 +390,6 @@ __device__ __forceinline__ bool relax_node_eval(const RelaxNode& nd, double g, d
   const double dy = nd.Y0 - (gam - 1.0) * dK;
   dD = (nd.X0 * (gam * l1px - l1py) + dy * (y - x) * iy) * inv_gm1 + dK;
   return true;
-}
-
-// Taylor coefficients in g of D_n(g)/rho_n up to g^kSeries for one node (index k
-// of Dk; Dk[0] = Dk[1] = 0).  With x = g X0, q = 1/(1 + g X0) = sum (-X0)^k g^k,
-// K = g^2 V2 q/2, y = g Y0 - (gam-1) K and L = log1p(y) from (1+y) L' = y':
-//   L_n = y_n - (1/n) sum_{j=1}^{n-1} (n-j) y_j L_{n-j},
-//   phi_k = (-1)^k X0^k/(k(k-1)),  psi_k = y_k - L_k,  (x log1p y)_k = X0 L_{k-1},
-//   D_k = [gam phi_k + psi_k - X0 L_{k-1}]/(gam-1) + K_k.
-// The leading coefficient is D_2 = [(gam-1) X0^2 + (X0 - Y0)^2]/(2(gam-1)) + V2/2.
-// Used where every |X0|, |Y0|, sqrt(V2) of the element is below 1e-4: then up to
-// g = 8 each further order is smaller by < 1e-3 and the truncation after g^8 is
-// below 1e-20 of the leading term.
-constexpr int kSeries = 8;
-__device__ __forceinline__ void relax_node_series(const RelaxNode& nd, double gam, double inv_gm1,
-                                                  double Dk[kSeries + 1]) {
-  double y[kSeries + 1], L[kSeries + 1], K[kSeries + 1];
-  const double mX = -nd.X0;
-  double pw = 1.0;  // (-X0)^(k-2)
-  K[0] = K[1] = 0.0;
-  for (int k = 2; k <= kSeries; ++k) {
-    K[k] = 0.5 * nd.V2 * pw;
-    pw *= mX;
-  }
-  y[0] = 0.0;
-  y[1] = nd.Y0;
-  for (int k = 2; k <= kSeries; ++k) y[k] = -(gam - 1.0) * K[k];
-  L[0] = 0.0;
-  for (int n = 1; n <= kSeries; ++n) {
-    double s = 0.0;
-    for (int j = 1; j < n; ++j) s = fma(double(n - j) * y[j], L[n - j], s);
-    L[n] = y[n] - s / double(n);
-  }
-  double xk = nd.X0 * nd.X0;  // X0^k, k = 2
-  double sgn = 1.0;           // (-1)^k
-  Dk[0] = Dk[1] = 0.0;
-  for (int k = 2; k <= kSeries; ++k) {
-    const double phi = sgn * xk / double(k * (k - 1));
-    Dk[k] = (gam * phi + (y[k] - L[k]) - nd.X0 * L[k - 1]) * inv_gm1 + K[k];
-    xk *= nd.X0;
-    sgn = -sgn;
-  }
 }
 
 // ---------------------------------------------------------------------------

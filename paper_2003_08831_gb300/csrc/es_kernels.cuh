@@ -18,6 +18,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "es_device.cuh"
 #include "es_launch.h"
 
@@ -115,15 +117,15 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
     const double p = (gam - 1.0) * (y[4] - 0.5 * rho * (v0 * v0 + v1 * v1 + v2 * v2));
     if (!(rho > 0.0) || !(p > 0.0)) atomicOr(status, kStatusNonphysical);
     // z1 = sqrt(rho/p) = rho / sqrt(rho p), z5 = sqrt(rho p)
-    if constexpr (sizeof(TF) == 8) {
+    if constexpr (std::is_same<TF, double>::value || std::is_same<TF, ff>::value) {
       const double rs = rsqrt(rho * p);
       const double z1 = rho * rs;
-      aux[0 * N + g] = z1;
-      aux[1 * N + g] = z1 * v0;
-      aux[2 * N + g] = z1 * v1;
-      aux[3 * N + g] = z1 * v2;
-      aux[4 * N + g] = rho * p * rs;
-      aux[5 * N + g] = p * rs;  // 1/z1 = sqrt(p/rho)
+      aux[0 * N + g] = TF(z1);
+      aux[1 * N + g] = TF(z1 * v0);
+      aux[2 * N + g] = TF(z1 * v1);
+      aux[3 * N + g] = TF(z1 * v2);
+      aux[4 * N + g] = TF(rho * p * rs);
+      aux[5 * N + g] = TF(p * rs);  // 1/z1 = sqrt(p/rho)
     } else {
       const float rf = float(rho), pf = float(p);
       const float rs = rsqrtf(rf * pf);
@@ -229,9 +231,9 @@ __global__ void __launch_bounds__(THREADS) k_grad(Params P, const TF* __restrict
 #pragma unroll
       for (int j = 0; j < P1; ++j) {
         const int nj = el * Np + line_node<P1>(m, a, b, j);
-        const TF Dij = TF(P.D[im * P1 + j]);
+        const TF Dij = Tab<TF>::D(P, im * P1 + j);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] += Dij * ws[c * EPB * Np + nj];
+        for (int c = 0; c < 4; ++c) fma_acc(acc[c], Dij, ws[c * EPB * Np + nj]);
       }
       if (im == P1 - 1 || im == 0) {
         const bool right = (im == P1 - 1);
@@ -321,11 +323,11 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
         for (int j = i + 1; j < P1; ++j) {
           TF f[5];
           ec_flux(z[i], z[j], m, C, f);
-          const TF dij = TF(P.D2[i * P1 + j]), dji = TF(P.D2[j * P1 + i]);
+          const TF dij = Tab<TF>::D2(P, i * P1 + j), dji = Tab<TF>::D2(P, j * P1 + i);
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
-            r[i][v] += dij * f[v];
-            r[j][v] += dji * f[v];
+            fma_acc(r[i][v], dij, f[v]);
+            fma_acc(r[j][v], dji, f[v]);
           }
         }
       }
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
           for (int i = 0; i < P1; ++i) {
             TF s = TF(0);
 #pragma unroll
-            for (int j = 0; j < P1; ++j) s += TF(P.D[i * P1 + j]) * fl[j];
+            for (int j = 0; j < P1; ++j) fma_acc(s, Tab<TF>::D(P, i * P1 + j), fl[j]);
             if (i == P1 - 1) s += TF(0.5) * iw * (f_next - fl[P1 - 1]);
             if (i == 0) s -= TF(0.5) * iw * (f_prev - fl[0]);
             r[i][1 + c] -= s;
@@ -510,68 +512,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
     else A = sr.A[e];
     double gk = __longlong_as_double(0x7ff0000000000000LL);  // +inf: unconstrained
     const double delta = sqrt(2.0 * a / ssum);
-    double mx = 0.0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) mx = fmax(mx, fmax(fmax(fabs(nd[r].X0), fabs(nd[r].Y0)), sqrt(nd[r].V2)));
-    const bool series = warp_max(mx) <= 1e-4;
-    if (delta > sr.delta_floor && A < 0.0 && series) {
-      // small changes: r(g) = sum_k C_k g^k + A g from per-node Taylor coefficients,
-      // then Newton on the polynomial (scalar, every lane identical)
-      double C[kSeries + 1];
-#pragma unroll
-      for (int k = 0; k <= kSeries; ++k) C[k] = 0.0;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (nd[r].c != 0.0) {
-          double Dk[kSeries + 1];
-          relax_node_series(nd[r], gam, inv_gm1, Dk);
-#pragma unroll
-          for (int k = 2; k <= kSeries; ++k) C[k] = fma(nd[r].c, Dk[k], C[k]);
-        }
-      }
-#pragma unroll
-      for (int k = 2; k <= kSeries; ++k) C[k] = warp_sum(C[k]);
-      double lo = 0.0, hi = sr.gamma_max;
-      bool hi_known = false;
-      double gcur = fmin(fmax(-A / a, 1e-3), sr.gamma_max);
-      for (int it = 0; it < 200; ++it) {
-        double rv = C[kSeries], dv = kSeries * C[kSeries];
-        for (int k = kSeries - 1; k >= 2; --k) {
-          rv = fma(rv, gcur, C[k]);
-          dv = fma(dv, gcur, k * C[k]);
-        }
-        rv = (rv * gcur + A) * gcur;  // sum_{k>=2} C_k g^k + A g
-        dv = dv * gcur + A;
-        if (rv > 0.0) {
-          hi = gcur;
-          hi_known = true;
-        } else {
-          lo = gcur;
-        }
-        const double step = rv / dv;
-        const double newton = gcur - step;
-        if (dv > 0.0 && fabs(step) <= 8.881784197001252e-16 * fmax(1.0, gcur)) {
-          gk = fmin(fmax(newton, lo), hi);
-          break;
-        }
-        if (rv == 0.0) {
-          gk = gcur;
-          break;
-        }
-        if (hi - lo <= 8.881784197001252e-16 * fmax(1.0, gcur)) {
-          gk = lo;
-          break;
-        }
-        const bool nok = dv > 0.0 && isfinite(newton) && newton > lo && newton < hi;
-        if (nok) gcur = newton;
-        else if (!hi_known) gcur = (gcur >= sr.gamma_max) ? sr.gamma_max : fmin(2.0 * gcur, sr.gamma_max);
-        else gcur = 0.5 * (lo + hi);
-        if (!hi_known && lo >= sr.gamma_max) {
-          gk = sr.gamma_max;
-          break;
-        }
-      }
-    } else if (delta > sr.delta_floor) {
+    if (delta > sr.delta_floor) {
       if (!(A < 0.0)) {
         if (lane == 0) atomicOr(sr.status, kStatusNoRoot);
       } else {

@@ -52,12 +52,12 @@ def random_state(mesh, seed, amp=0.2, noise=0.02):
     return inputs.conserved(field(1.0, amp), field(0.3, amp), field(-0.2, amp), field(0.1, amp), field(1.0, amp), G)
 
 
-def assert_rhs_close(got, ref, terms):
+def assert_rhs_close(got, ref, terms, eps=EPS):
     got = np.asarray(got).reshape(5, -1)
     ref = np.asarray(ref).reshape(5, -1)
     terms = np.asarray(terms).reshape(5, -1)
     scale = np.maximum(np.max(np.abs(ref), axis=1), 1e-3 * np.max(np.abs(ref)))[:, None]
-    bound = np.maximum(TOL * scale, 256 * EPS * terms)
+    bound = np.maximum(TOL * scale, 256 * eps * terms)
     bad = np.abs(got - ref) > bound
     assert not bad.any(), (np.argwhere(bad)[:5], np.max(np.abs(got - ref) / bound))
 
@@ -121,7 +121,7 @@ def vortex_setup(N=4, p=3, nz=None):
     return mesh, U, lo, hi
 
 
-def gamma_sensitivity(mesh, U, dt, nsteps, phys, tab, mode, hist, seeds=4):
+def gamma_sensitivity(mesh, U, dt, nsteps, phys, tab, mode, hist, seeds=4, eps=EPS):
     """Relative change of each step's gamma and of the last gamma_kappa when every
     right-hand side evaluation of the oracle is perturbed at its rounding level
     (2 eps times the magnitude of the summed terms, per node).  gamma_kappa is a
@@ -136,7 +136,7 @@ def gamma_sensitivity(mesh, U, dt, nsteps, phys, tab, mode, hist, seeds=4):
         def noisy(m_, U_, p_):
             R = dg.rhs(m_, U_, p_)
             T = dg.rhs_term_magnitude(m_, U_, p_)
-            return R + 2 * EPS * T * rng.standard_normal(R.shape)
+            return R + 2 * eps * T * rng.standard_normal(R.shape)
         _, _, h2 = rk.advance(mesh, U, dt, nsteps, phys, tab, mode=mode, rhs=noisy)
         dg_ = np.maximum(dg_, np.abs(np.array([h.gamma for h in h2]) - g0) / g0)
         gk2 = h2[-1].gamma_kappa.reshape(-1)
@@ -145,13 +145,13 @@ def gamma_sensitivity(mesh, U, dt, nsteps, phys, tab, mode, hist, seeds=4):
     return dg_, dgk
 
 
-def compare_advance(mesh, U, lo, hi, phys, tabname, nsteps, mode="local", cfl=0.5, **kw):
+def compare_advance(mesh, U, lo, hi, phys, tabname, nsteps, mode="local", cfl=0.5, eps=EPS, **kw):
     """FP64 parity of es_advance: state at 1e-12 per variable; gamma and gamma_kappa at
     1e-12 or, where larger, 8x their measured sensitivity to last-bit RHS changes."""
     from paper_2003_08831_gb300 import _binding as B
     dt = rk.stable_dt(mesh, U, phys, cfl)
     Uo, to, hist = rk.advance(mesh, U, dt, nsteps, phys, rk.TABLEAUX[tabname], mode=mode)
-    sens_g, sens_gk = gamma_sensitivity(mesh, U, dt, nsteps, phys, rk.TABLEAUX[tabname], mode, hist)
+    sens_g, sens_gk = gamma_sensitivity(mesh, U, dt, nsteps, phys, rk.TABLEAUX[tabname], mode, hist, eps=eps)
     relax_mode = {"local": B.ES_RELAX_LOCAL, "global": B.ES_RELAX_GLOBAL, "none": B.ES_RELAX_NONE}[mode]
     s = solver(mesh.p, mesh.n, lo, hi, mu=phys.mu, Pr=phys.Pr, interface_diss=phys.diss,
                rk=B.ES_RK_BS3 if tabname == "BS3" else B.ES_RK_RK4, relax=relax_mode, **kw)
