@@ -168,6 +168,10 @@ void build_params(const es_config& C, Params* out) {
   P.gam = C.gamma_gas;
   P.mu = C.mu;
   P.R = C.R;
+  P.inv_R = 1.0 / C.R;
+  P.Cd = FluxConst<double>::make(C.gamma_gas);
+  P.Cf = FluxConst<float>::make(C.gamma_gas);
+  P.Cff = FluxConst<ff>::make(C.gamma_gas);
   P.kappa_heat = C.mu > 0.0 ? C.mu * C.gamma_gas * C.R / ((C.gamma_gas - 1.0) * C.Pr) : 0.0;
   P.K = C.nx * C.ny * C.nz;
   P.diss = C.interface_diss;

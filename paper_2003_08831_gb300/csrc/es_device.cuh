@@ -27,6 +27,23 @@ struct InstGeom {
   double dt;            // the instance's time step
 };
 
+// Constants of the gas law used by the flux, in the flux's precision.
+template <typename T>
+struct FluxConst {
+  T gam, gm1, inv_gm1, sqrt_gam;
+  T C1x, C2x;  // 4 c1 gam/(gam-1), c2 gam/(gam-1) with c1 = (gam+1)/(2 gam), c2 = (gam-1)/(2 gam)
+  __host__ __device__ static FluxConst make(double g) {
+    FluxConst c;
+    c.gam = T(g);
+    c.gm1 = T(g - 1.0);
+    c.inv_gm1 = T(1.0 / (g - 1.0));
+    c.sqrt_gam = T(sqrt(g));
+    c.C1x = T(4.0 * (g + 1.0) / (2.0 * g) * g / (g - 1.0));
+    c.C2x = T((g - 1.0) / (2.0 * g) * g / (g - 1.0));
+    return c;
+  }
+};
+
 // Operator tables and physics constants, passed by value to every kernel.
 struct Params {
   double D[kMaxP1 * kMaxP1];   // SBP derivative on [-1, 1], row-major
@@ -37,6 +54,10 @@ struct Params {
   double inv_omega_end;        // 1/omega_0 = 1/omega_p
   double gam;                  // ratio of specific heats
   double mu, kappa_heat, R;    // viscosity, heat conductivity mu c_p / Pr, gas constant
+  double inv_R;                // 1/R
+  FluxConst<double> Cd;        // flux constants per precision (host-computed: no
+  FluxConst<float> Cf;         // divisions or square roots in the kernels)
+  FluxConst<ff> Cff;
   int K;                       // elements in the group
   int diss;                    // Rusanov interface dissipation on/off
   int p1;                      // p + 1
@@ -45,6 +66,11 @@ struct Params {
   const InstGeom* geom;        // device table [ninst] (batches), or null
   const int* elem_inst;        // device [K]: instance of each element (batches), or null
 };
+
+template <typename T> __device__ __forceinline__ const FluxConst<T>& flux_const(const Params& P);
+template <> __device__ __forceinline__ const FluxConst<double>& flux_const<double>(const Params& P) { return P.Cd; }
+template <> __device__ __forceinline__ const FluxConst<float>& flux_const<float>(const Params& P) { return P.Cf; }
+template <> __device__ __forceinline__ const FluxConst<ff>& flux_const<ff>(const Params& P) { return P.Cff; }
 
 // ---------------------------------------------------------------------------
 // element / node index helpers
@@ -143,22 +169,6 @@ __device__ __forceinline__ bool below(double u, double eps) {
   return __double_as_longlong(u) < __double_as_longlong(eps);
 }
 __device__ __forceinline__ bool below(float u, float eps) { return __float_as_int(u) < __float_as_int(eps); }
-
-// Constants of the gas law used by the flux, in the flux's precision.
-template <typename T>
-struct FluxConst {
-  T gam, inv_gm1, sqrt_gam;
-  T C1x, C2x;  // 4 c1 gam/(gam-1), c2 gam/(gam-1) with c1 = (gam+1)/(2 gam), c2 = (gam-1)/(2 gam)
-  __host__ __device__ static FluxConst make(double g) {
-    FluxConst c;
-    c.gam = T(g);
-    c.inv_gm1 = T(1.0 / (g - 1.0));
-    c.sqrt_gam = T(sqrt(g));
-    c.C1x = T(4.0 * (g + 1.0) / (2.0 * g) * g / (g - 1.0));
-    c.C2x = T((g - 1.0) / (2.0 * g) * g / (g - 1.0));
-    return c;
-  }
-};
 
 // Ismail--Roe two-point flux in direction m between states a and b.
 // With S = a + b, D = a - b for z1 and z5, the two logarithmic means enter only

@@ -24,15 +24,80 @@ using ::fabs;
 using ::fmax;
 using ::log;
 
+struct ff;
+__device__ __forceinline__ ff ff_from_double(double d);
+__device__ __forceinline__ double ff_to_double(float hi, float lo);
+
 struct __align__(8) ff {
   float hi, lo;
   ff() = default;
   __host__ __device__ constexpr ff(float h, float l) : hi(h), lo(l) {}
-  // split of a double: hi = fl32(d), lo = fl32(d - hi) (exact difference in FP64)
-  __host__ __device__ explicit ff(double d) : hi(float(d)), lo(float(d - double(float(d)))) {}
+  // split of a double (device: on the integer pipe, see ff_from_double;
+  // host: hi = fl32(d), lo = fl32(d - hi))
+  __host__ __device__ explicit ff(double d);
   __host__ __device__ explicit ff(int i) : hi(float(i)), lo(0.0f) {}
-  __host__ __device__ explicit operator double() const { return double(hi) + double(lo); }
+  __host__ __device__ explicit operator double() const;
 };
+
+// float -> double by placing the bits (exact; no FP64 instruction).  Zero keeps its
+// sign; subnormal, infinite and NaN inputs take the conversion instruction.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e - 1u < 254u) {
+    const unsigned hi32 = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double(int(hi32), int(u << 29));
+  }
+  if ((u << 1) == 0u) return __hiloint2double(int(u & 0x80000000u), 0);
+  return double(f);
+}
+
+// double -> float-float on the integer and FP32 pipes: hi = d with its significand
+// truncated to 24 bits (exact in FP32), lo = the remaining 29 significand bits rounded
+// to 24 (one FP32 rounding): |hi + lo - d| <= 2^-48 |d|.  The fast path covers
+// 2^-74 <= |d| < 2^127 and zero; other magnitudes use the FP64 conversions.
+__device__ __forceinline__ ff ff_from_double(double d) {
+  const unsigned h = unsigned(__double_as_longlong(d) >> 32);
+  const unsigned l = unsigned(__double_as_longlong(d));
+  const unsigned e = (h >> 20) & 0x7FFu;
+  const unsigned sign = h & 0x80000000u;
+  if (e - 949u < 202u) {
+    const float hi = __uint_as_float(sign | ((e - 896u) << 23) | ((h & 0xFFFFFu) << 3) | (l >> 29));
+    // m29 = 2^6 a + b, a < 2^23, b < 2^6: both exact as floats (magic-number conversion),
+    // one fma rounds 64 a + b to 24 bits, the power-of-two scale 2^(e - 1075) is exact
+    const unsigned m29 = l & 0x1FFFFFFFu;
+    const float a = __fsub_rn(__uint_as_float(0x4B000000u | (m29 >> 6)), 8388608.0f);
+    const float b = __fsub_rn(__uint_as_float(0x4B000000u | (m29 & 63u)), 8388608.0f);
+    const float m = __fmaf_rn(a, 64.0f, b);
+    const float scale = __uint_as_float(sign | ((e - 948u) << 23));
+    return ff(hi, __fmul_rn(m, scale));
+  }
+  if (((h << 1) | l) == 0u) return ff(__uint_as_float(sign), 0.0f);
+  const float hi = __double2float_rn(d);
+  return ff(hi, __double2float_rn(d - double(hi)));
+}
+
+// float-float -> double: both parts placed exactly, one FP64 addition rounds the sum
+__device__ __forceinline__ double ff_to_double(float hi, float lo) {
+  return f32_to_f64_bits(hi) + f32_to_f64_bits(lo);
+}
+
+__host__ __device__ inline ff::ff(double d) {
+#ifdef __CUDA_ARCH__
+  *this = ff_from_double(d);
+#else
+  hi = float(d);
+  lo = float(d - double(hi));
+#endif
+}
+
+__host__ __device__ inline ff::operator double() const {
+#ifdef __CUDA_ARCH__
+  return ff_to_double(hi, lo);
+#else
+  return double(hi) + double(lo);
+#endif
+}
 
 // s + e = a + b exactly (Knuth's TwoSum, 6 operations, no condition on a, b)
 __device__ __forceinline__ ff two_sum(float a, float b) {

@@ -80,15 +80,95 @@ __device__ __forceinline__ void entropy_var_increment(const double u[5], const d
 }
 
 // ---------------------------------------------------------------------------
+// Float-float pieces of the stage preparation in the mixed and ES_FP64X modes:
+// the parameter vector and the entropy-variable increments on the FP32 pipe
+// (es_ff.cuh), the FP64 state only read and split.
+__device__ __forceinline__ ff ff_half(ff x) { return ff(0.5f * x.hi, 0.5f * x.lo); }
+__device__ __forceinline__ ff ff_twice(ff x) { return ff(2.0f * x.hi, 2.0f * x.lo); }
+
+// log(1 + z) - z for |z| <= 1e-3: z^2 (-1/2 + z/3 + tail) with z^2, z/3 and the sum in
+// float-float and the tail -z^2/4 + z^3/5 - z^4/6 + z^5/7 (below 5e-7 of the 1/2) in
+// FP32, so the result carries ~2^-47 relative error; larger |z| through FP64.
+__device__ __forceinline__ ff ff_log1pmx(ff z) {
+  if (fabsf(z.hi) <= 1e-3f) {
+    const float t = z.hi;
+    float tail = __fmaf_rn(t, 1.0f / 7.0f, -1.0f / 6.0f);
+    tail = __fmaf_rn(tail, t, 0.2f);
+    tail = __fmaf_rn(tail, t, -0.25f);
+    tail = __fmul_rn(tail, __fmul_rn(t, t));
+    constexpr float th = float(1.0 / 3.0);
+    constexpr float tl = float(1.0 / 3.0 - double(th));
+    const float pz = __fmul_rn(z.hi, th);
+    float ez = __fmaf_rn(z.hi, th, -pz);
+    ez = __fmaf_rn(z.hi, tl, ez);
+    ez = __fmaf_rn(z.lo, th, ez);
+    const ff s = fast_two_sum(-0.5f, pz);
+    const ff poly = fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(ez, tail)));
+    return (z * z) * poly;
+  }
+  return ff(log1pmx(double(z)));
+}
+
+// 1/sqrt(x): the FP32 approximation r (rsqrt.approx.ftz.f32, ~2^-23) refined with the
+// residual t = 1 - x r^2 formed in float-float (r^2 exact by TwoProd) by the
+// second-order step r (1 + t/2 + 3 t^2/8).
+__device__ __forceinline__ ff ff_rsqrt(ff x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x.hi));
+  const float r2 = __fmul_rn(r, r);
+  const float r2l = __fmaf_rn(r, r, -r2);
+  const float pp = __fmul_rn(x.hi, r2);
+  float e = __fmaf_rn(x.hi, r2, -pp);
+  e = __fmaf_rn(x.hi, r2l, e);
+  e = __fmaf_rn(x.lo, r2, e);
+  const float t = __fsub_rn(__fsub_rn(1.0f, pp), e);
+  const float c = __fmul_rn(__fmul_rn(r, t), __fmaf_rn(0.375f, t, 0.5f));
+  return fast_two_sum(r, c);
+}
+
+// w(u + e) - w(u) in float-float (same formulas as entropy_var_increment)
+__device__ __forceinline__ void entropy_var_increment_ff(const ff u[5], const ff e[5], const FluxConst<ff>& C,
+                                                         ff dw[5]) {
+  const ff one(1.0f, 0.0f);
+  const ff rho = u[0];
+  const ff rho1 = rho + e[0];
+  const ff m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+  const ff Pr = C.gm1 * (rho * u[4] - ff_half(m2));
+  const ff inv = ff_rcp(rho * rho1 * Pr);
+  const ff ir = rho1 * Pr * inv, ir1 = rho * Pr * inv, ip = rho * rho * rho1 * inv;
+  const ff v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
+  const ff v2s = v0 * v0 + v1 * v1 + v2 * v2;
+  const ff x = e[0] * ir;
+  const ff d0 = (e[1] - v0 * e[0]) * ir1, d1 = (e[2] - v1 * e[0]) * ir1, d2 = (e[3] - v2 * e[0]) * ir1;
+  const ff dv2 = d0 * d0 + d1 * d1 + d2 * d2;
+  const ff y = C.gm1 * (e[4] - (v0 * e[1] + v1 * e[2] + v2 * e[3]) + ff_half(v2s * e[0]) - ff_half(rho1 * dv2)) * ip;
+  const ff beta = rho * ip;
+  const ff iy = ff_rcp(one + y);
+  const ff ds = (y + ff_log1pmx(y)) - C.gam * (x + ff_log1pmx(x));
+  const ff xy = x - y;
+  const ff opx = one + x;
+  const ff dkin = ff_half(beta * (xy * v2s + opx * (ff_twice(v0 * d0 + v1 * d1 + v2 * d2) + dv2)) * iy);
+  dw[0] = -(ds * C.inv_gm1) - dkin;
+  dw[1] = beta * (xy * v0 + opx * d0) * iy;
+  dw[2] = beta * (xy * v1 + opx * d1) * iy;
+  dw[3] = beta * (xy * v2 + opx * d2) * iy;
+  dw[4] = -(beta * xy * iy);
+}
+
+// ---------------------------------------------------------------------------
 // y = u (+ gamma d when the instance has a pending relaxed update and this is the
 // step's first stage) + dt sum_j a_ij k_j; NPREV stages enter (compile time).
+// FP64 mode: everything in FP64.  Mixed and ES_FP64X: the FP64 state is split into
+// float-float (integer pipe), the stage increment e = dt sum_j a_ij k_j, y = u + e,
+// the parameter vector and w(y) - w(u) are formed in float-float on the FP32 pipe
+// (the mixed mode rounds z to FP32 for its fluxes).
 template <typename TF, int NPREV>
 __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __restrict__ status) {
   const long long N = (long long)P.K * sp.Np;
   const double gam = P.gam;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
     const int inst = inst_of(P, int(g / sp.Np));
-    double u[5], y[5];
+    double u[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = sp.q[v * N + g];
     if (sp.pending && sp.pending[inst]) {
@@ -99,51 +179,87 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
         sp.q[v * N + g] = u[v];
       }
     }
+    if constexpr (std::is_same<TF, double>::value) {
+      double y[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) y[v] = u[v];
-    if constexpr (NPREV > 0) {
-      const double dt = geom_of(P, inst).dt;
+      for (int v = 0; v < 5; ++v) y[v] = u[v];
+      if constexpr (NPREV > 0) {
+        const double dt = geom_of(P, inst).dt;
 #pragma unroll
-      for (int j = 0; j < NPREV; ++j) {
-        const double c = sp.coef[j] * dt;
-        const double* kj = sp.k[j];
+        for (int j = 0; j < NPREV; ++j) {
+          const double c = sp.coef[j] * dt;
+          const double* kj = sp.k[j];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) y[v] = fma(c, kj[v * N + g], y[v]);
+          for (int v = 0; v < 5; ++v) y[v] = fma(c, kj[v * N + g], y[v]);
+        }
       }
-    }
-    const double rho = y[0];
-    const double ir = fast_rcp(rho);
-    const double v0 = y[1] * ir, v1 = y[2] * ir, v2 = y[3] * ir;
-    const double p = (gam - 1.0) * (y[4] - 0.5 * rho * (v0 * v0 + v1 * v1 + v2 * v2));
-    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(status, kStatusNonphysical);
-    // z1 = sqrt(rho/p) = rho / sqrt(rho p), z5 = sqrt(rho p)
-    if constexpr (std::is_same<TF, double>::value || std::is_same<TF, ff>::value) {
+      const double rho = y[0];
+      const double ir = fast_rcp(rho);
+      const double v0 = y[1] * ir, v1 = y[2] * ir, v2 = y[3] * ir;
+      const double p = (gam - 1.0) * (y[4] - 0.5 * rho * (v0 * v0 + v1 * v1 + v2 * v2));
+      if (!(rho > 0.0) || !(p > 0.0)) atomicOr(status, kStatusNonphysical);
+      // z1 = sqrt(rho/p) = rho / sqrt(rho p), z5 = sqrt(rho p)
       const double rs = rsqrt(rho * p);
       const double z1 = rho * rs;
-      aux[0 * N + g] = TF(z1);
-      aux[1 * N + g] = TF(z1 * v0);
-      aux[2 * N + g] = TF(z1 * v1);
-      aux[3 * N + g] = TF(z1 * v2);
-      aux[4 * N + g] = TF(rho * p * rs);
-      aux[5 * N + g] = TF(p * rs);  // 1/z1 = sqrt(p/rho)
-    } else {
-      const float rf = float(rho), pf = float(p);
-      const float rs = rsqrtf(rf * pf);
-      const float z1 = rf * rs;
       aux[0 * N + g] = z1;
-      aux[1 * N + g] = z1 * float(v0);
-      aux[2 * N + g] = z1 * float(v1);
-      aux[3 * N + g] = z1 * float(v2);
-      aux[4 * N + g] = rf * pf * rs;
-      aux[5 * N + g] = pf * rs;
-    }
-    if (sp.dw) {
-      double e[5], dw[5];
+      aux[1 * N + g] = z1 * v0;
+      aux[2 * N + g] = z1 * v1;
+      aux[3 * N + g] = z1 * v2;
+      aux[4 * N + g] = rho * p * rs;
+      aux[5 * N + g] = p * rs;  // 1/z1 = sqrt(p/rho)
+      if (sp.dw) {
+        double e[5], dw[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) e[v] = y[v] - u[v];
-      entropy_var_increment(u, e, gam, 1.0 / (gam - 1.0), dw);
+        for (int v = 0; v < 5; ++v) e[v] = y[v] - u[v];
+        entropy_var_increment(u, e, gam, P.Cd.inv_gm1, dw);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sp.dw[v * N + g] = dw[v];
+        for (int v = 0; v < 5; ++v) sp.dw[v * N + g] = dw[v];
+      }
+    } else {
+      const FluxConst<ff>& C = P.Cff;
+      ff uf[5], ef[5], yf[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        uf[v] = ff_from_double(u[v]);
+        ef[v] = ff(0.0f, 0.0f);
+      }
+      if constexpr (NPREV > 0) {
+        const double dt = geom_of(P, inst).dt;
+#pragma unroll
+        for (int j = 0; j < NPREV; ++j) {
+          const ff c = ff_from_double(sp.coef[j] * dt);
+          const double* kj = sp.k[j];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) ff_fma_acc(ef[v], c, ff_from_double(kj[v * N + g]));
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          ef[v] = ff_norm(ef[v]);
+          yf[v] = uf[v] + ef[v];
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) yf[v] = uf[v];
+      }
+      const ff rho = yf[0];
+      const ff ir = ff_rcp(rho);
+      const ff v0 = yf[1] * ir, v1 = yf[2] * ir, v2 = yf[3] * ir;
+      const ff p = C.gm1 * (yf[4] - ff_half(yf[1] * v0 + yf[2] * v1 + yf[3] * v2));
+      if (!(rho.hi > 0.0f) || !(p.hi > 0.0f)) atomicOr(status, kStatusNonphysical);
+      const ff rs = ff_rsqrt(rho * p);
+      const ff z1 = rho * rs;
+      const ff z[6] = {z1, z1 * v0, z1 * v1, z1 * v2, rho * p * rs, p * rs};
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        if constexpr (std::is_same<TF, ff>::value) aux[c * N + g] = z[c];
+        else aux[c * N + g] = __fadd_rn(z[c].hi, z[c].lo);
+      }
+      if (sp.dw) {
+        ff dw[5];
+        entropy_var_increment_ff(uf, ef, C, dw);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sp.dw[v * N + g] = double(dw[v]);
+      }
     }
   }
 }
@@ -162,7 +278,7 @@ __global__ void k_face(Params P, const TF* __restrict__ aux, TF* __restrict__ F)
   constexpr int P2 = P1 * P1, Np = P1 * P2;
   const long long N = (long long)P.K * Np;
   const long long total = 3LL * P.K * P2;
-  const FluxConst<TF> C = FluxConst<TF>::make(P.gam);
+  const FluxConst<TF> C = flux_const<TF>(P);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const int m = int(idx / ((long long)P.K * P2));
@@ -204,7 +320,7 @@ __global__ void __launch_bounds__(THREADS) k_grad(Params P, const TF* __restrict
   const int e0 = blockIdx.x * EPB;
   const int nel = min(EPB, P.K - e0);
   const int nn = nel * Np;
-  const TF mu = TF(P.mu), kap = TF(P.kappa_heat), iR = TF(1.0 / P.R);
+  const TF mu = TF(P.mu), kap = TF(P.kappa_heat), iR = TF(P.inv_R);
   const TF iw = TF(P.inv_omega_end);
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
     const long long g = (long long)e0 * Np + t;
@@ -289,7 +405,7 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
   const int e0 = blockIdx.x * EPB;
   const int nel = min(EPB, P.K - e0);
   const int nn = nel * Np;
-  const FluxConst<TF> C = FluxConst<TF>::make(P.gam);
+  const FluxConst<TF> C = flux_const<TF>(P);
   const TF iw = TF(P.inv_omega_end);
 
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {

@@ -164,7 +164,8 @@ def compare_advance(mesh, U, lo, hi, phys, tabname, nsteps, mode="local", cfl=0.
     gh = gh.cpu().numpy()
     tol_g = np.maximum(TOL, 8 * sens_g)
     assert np.all(np.abs(gh - gref) / gref <= tol_g), (gh, gref, tol_g)
-    assert abs(t.item() - to) < TOL * to
+    # t = t0 + sum_n gamma_n dt (Eq. (t-n-gamma)): its bound is the sum of the gamma bounds
+    assert abs(t.item() - to) <= max(TOL * to, dt * np.sum(tol_g * gref))
     gko = hist[-1].gamma_kappa.reshape(-1)
     gkg = gk.cpu().numpy()
     fin = np.isfinite(gko)
