@@ -206,7 +206,7 @@ struct Group {
   int vol_variant = 0;
   std::vector<InstGeom> geom;      // host copy of the instance table
   std::vector<int> inst_ids;       // batch instance index of each local instance
-  double* k[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* k[4] = {nullptr, nullptr, nullptr, nullptr};  // stage values, tf bytes each
   void* aux = nullptr;
   void* F = nullptr;
   void* fV = nullptr;
@@ -415,7 +415,7 @@ int group_init(Group& g, const es_config* insts, int n, int stages, bool own_sta
   const long long N = g.N;
   const long long P2 = (long long)g.P1 * g.P1;
   int rc = ES_OK;
-  for (int i = 0; i < stages && rc == ES_OK; ++i) rc = dev_alloc(&g.k[i], 5 * N);
+  for (int i = 0; i < stages && rc == ES_OK; ++i) rc = dev_alloc_bytes(&g.k[i], 5 * N * g.tf);
   if (rc == ES_OK) rc = dev_alloc_bytes(&g.aux, kAuxPlanes * N * g.tf);
   if (rc == ES_OK) rc = dev_alloc_bytes(&g.F, 15 * K * P2 * g.tf);
   if (rc == ES_OK && C.mu > 0.0) rc = dev_alloc_bytes(&g.fV, 12 * N * g.tf);
@@ -726,7 +726,7 @@ int es_rhs(es_ctx* c, const double* q, double* dqdt, double* E_elem, void* strea
   sp.Np = c->g.Np;
   StageVol sv;
   std::memset(&sv, 0, sizeof(sv));
-  sv.kout = dqdt;
+  sv.kout64 = dqdt;
   sv.E = E_elem;
   return run_stage(c->eng, c->g, sp, sv, st);
 }

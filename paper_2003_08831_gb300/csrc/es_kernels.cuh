@@ -83,6 +83,9 @@ __device__ __forceinline__ void entropy_var_increment(const double u[5], const d
 // Float-float pieces of the stage preparation in the mixed and ES_FP64X modes:
 // the parameter vector and the entropy-variable increments on the FP32 pipe
 // (es_ff.cuh), the FP64 state only read and split.
+__device__ __forceinline__ ff to_ff(ff x) { return x; }
+__device__ __forceinline__ ff to_ff(float x) { return ff(x, 0.0f); }
+__device__ __forceinline__ ff to_ff(double x) { return ff_from_double(x); }
 __device__ __forceinline__ ff ff_half(ff x) { return ff(0.5f * x.hi, 0.5f * x.lo); }
 __device__ __forceinline__ ff ff_twice(ff x) { return ff(2.0f * x.hi, 2.0f * x.lo); }
 
@@ -188,7 +191,7 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
 #pragma unroll
         for (int j = 0; j < NPREV; ++j) {
           const double c = sp.coef[j] * dt;
-          const double* kj = sp.k[j];
+          const double* kj = static_cast<const double*>(sp.k[j]);
 #pragma unroll
           for (int v = 0; v < 5; ++v) y[v] = fma(c, kj[v * N + g], y[v]);
         }
@@ -228,9 +231,9 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
 #pragma unroll
         for (int j = 0; j < NPREV; ++j) {
           const ff c = ff_from_double(sp.coef[j] * dt);
-          const double* kj = sp.k[j];
+          const TF* kj = static_cast<const TF*>(sp.k[j]);
 #pragma unroll
-          for (int v = 0; v < 5; ++v) ff_fma_acc(ef[v], c, ff_from_double(kj[v * N + g]));
+          for (int v = 0; v < 5; ++v) ff_fma_acc(ef[v], c, to_ff(kj[v * N + g]));
         }
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
@@ -496,38 +499,84 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
     const long long g = (long long)e0 * Np + t;
     const int n = t % Np;
     const InstGeom& G = geom_of(P, inst_of(P, e0 + t / Np));
-    double k[5];
+    const double Pn = mass_weight<P1>(P, G.J, n);
+    if constexpr (std::is_same<TF, double>::value) {
+      double k[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) k[v] = double(acc[v * EPB * Np + t]);
-    if (sv.d_out) {
-      const double dt = G.dt;
+      for (int v = 0; v < 5; ++v) k[v] = acc[v * EPB * Np + t];
+      if (sv.d_out) {
+        const double dt = G.dt;
+        const double* const* dk = reinterpret_cast<const double* const*>(sv.dk);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        double dv = (sv.dcoef_self * dt) * k[v];
-        for (int j = 0; j < sv.nd; ++j) dv = fma(sv.dcoef[j] * dt, sv.dk[j][v * N + g], dv);
-        sv.d_out[v * N + g] = dv;
+        for (int v = 0; v < 5; ++v) {
+          double dv = (sv.dcoef_self * dt) * k[v];
+          for (int j = 0; j < sv.nd; ++j) dv = fma(sv.dcoef[j] * dt, dk[j][v * N + g], dv);
+          sv.d_out[v * N + g] = dv;
+        }
+      } else {
+        double* ko = sv.kout64 ? sv.kout64 : static_cast<double*>(sv.kout);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ko[v * N + g] = k[v];
+      }
+      if (wantE) {
+        Zstate<TF> s;
+#pragma unroll
+        for (int c = 0; c < kAux; ++c) s.z[c] = za[c * EPB * Np + t];
+        TF w[5];
+        z_to_w(s, C, w);
+        double sum = 0.0;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sum += double(w[v]) * k[v];
+        red[t] = Pn * sum;
+      }
+      if (wantA) {
+        double sum = 0.0;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sum += sv.dw[v * N + g] * k[v];
+        red[EPB * Np + t] = Pn * G.dt * sum;
       }
     } else {
+      // mixed / float-float: k stays in the flux precision; d and the element sums are
+      // formed in float-float and joined to FP64 once
+      TF kt[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sv.kout[v * N + g] = k[v];
-    }
-    const double Pn = mass_weight<P1>(P, G.J, n);
-    if (wantE) {
-      Zstate<TF> s;
+      for (int v = 0; v < 5; ++v) kt[v] = acc[v * EPB * Np + t];
+      if (sv.d_out) {
+        const double dt = G.dt;
+        const ff cs = ff_from_double(sv.dcoef_self * dt);
+        ff cj[4];
+        for (int j = 0; j < sv.nd; ++j) cj[j] = ff_from_double(sv.dcoef[j] * dt);
 #pragma unroll
-      for (int c = 0; c < kAux; ++c) s.z[c] = za[c * EPB * Np + t];
-      TF w[5];
-      z_to_w(s, C, w);
-      double sum = 0.0;
+        for (int v = 0; v < 5; ++v) {
+          ff dv = cs * to_ff(kt[v]);
+          for (int j = 0; j < sv.nd; ++j) ff_fma_acc(dv, cj[j], to_ff(static_cast<const TF*>(sv.dk[j])[v * N + g]));
+          sv.d_out[v * N + g] = double(ff_norm(dv));
+        }
+      } else if (sv.kout64) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sum += double(w[v]) * k[v];
-      red[t] = Pn * sum;
-    }
-    if (wantA) {
-      double sum = 0.0;
+        for (int v = 0; v < 5; ++v) sv.kout64[v * N + g] = double(kt[v]);
+      } else {
+        TF* ko = static_cast<TF*>(sv.kout);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sum += sv.dw[v * N + g] * k[v];
-      red[EPB * Np + t] = Pn * G.dt * sum;
+        for (int v = 0; v < 5; ++v) ko[v * N + g] = kt[v];
+      }
+      if (wantE) {
+        Zstate<TF> s;
+#pragma unroll
+        for (int c = 0; c < kAux; ++c) s.z[c] = za[c * EPB * Np + t];
+        TF w[5];
+        z_to_w(s, C, w);
+        double sum = 0.0;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sum += double(w[v]) * double(kt[v]);
+        red[t] = Pn * sum;
+      }
+      if (wantA) {
+        ff sum(0.0f, 0.0f);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ff_fma_acc(sum, ff_from_double(sv.dw[v * N + g]), to_ff(kt[v]));
+        red[EPB * Np + t] = Pn * G.dt * double(ff_norm(sum));
+      }
     }
   }
   const bool doA = sv.A != nullptr && (wantA || sv.A_init);
@@ -573,7 +622,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
     const int inst = inst_of(P, e);
     const double J = geom_of(P, inst).J;
     RelaxNode nd[R];
-    double a_part = 0.0, s_part = 0.0, A_part = 0.0;
+    double a_part = 0.0, s_part = 0.0, A_part = 0.0, b_part = 0.0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = lane + 32 * r;
@@ -611,6 +660,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
         const double XY = nd[r].X0 - nd[r].Y0;
         a_part += 0.5 * nd[r].c * (nd[r].X0 * nd[r].X0 + XY * XY * inv_gm1 + nd[r].V2);
         s_part += nd[r].c;
+        b_part += nd[r].c * relax_node_cubic(nd[r], gam, inv_gm1);
         if (sr.u_new) {
           // A = sum P w(u).d - d_eta with w = ((gam - s)/(gam-1) - beta|v|^2/2, beta v, -beta)
           const double beta = rho * ip;
@@ -623,6 +673,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
     }
     const double a = warp_sum(a_part);
     const double ssum = warp_sum(s_part);
+    const double bcub = warp_sum(b_part);
     double A;
     if (sr.u_new) A = warp_sum(A_part) - sr.deta[e];
     else A = sr.A[e];
@@ -634,7 +685,12 @@ __global__ void k_relax(Params P, StageRelax sr) {
       } else {
         double lo = 0.0, hi = sr.gamma_max;
         bool hi_known = false;
-        double gcur = fmin(fmax(-A / a, 1e-3), sr.gamma_max);
+        // start: root of the cubic model a g^2 + b g^3 + A g (one Newton step on
+        // a + b g + A/g from the quadratic model's root -A/a), off by O(delta^2)
+        double gcur = -A / a;
+        const double den = a + 2.0 * bcub * gcur;
+        if (den > 0.0) gcur -= bcub * gcur * gcur / den;
+        gcur = fmin(fmax(gcur, 1e-3), sr.gamma_max);
         for (int it = 0; it < 100; ++it) {
           double sr_ = 0.0, sd_ = 0.0;
           bool ok = true;

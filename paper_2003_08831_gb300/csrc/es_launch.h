@@ -22,18 +22,19 @@ struct StagePrep {
   const int* pending;       // per instance: relaxed update u += gamma d not yet applied (nullptr: none)
   int nprev;
   double coef[4];           // a_ij (multiplied by the instance's dt in the kernel)
-  const double* k[4];
+  const void* k[4];         // stage values in the flux precision (double, float or float-float)
   double* dw;               // w(y) - w(u) output, or nullptr
   int Np;
 };
 
 // k_volume outputs
 struct StageVol {
-  double* kout;        // k_i = f(y^i) (unless d_out is set)
+  void* kout;          // k_i = f(y^i) in the flux precision (unless d_out or kout64 is set)
+  double* kout64;      // k_i = f(y^i) in FP64 (the right-hand-side entry points)
   double* d_out;       // last stage: d = dt (dcoef_self k_i + sum_j dcoef[j] dk[j]) instead of k_i
   int nd;
   double dcoef[4];     // b_j
-  const double* dk[4];
+  const void* dk[4];   // earlier stages' k in the flux precision
   double dcoef_self;   // b_i
   double* E;           // (eta' f)(y^i) per element, or nullptr
   const double* dw;    // w(y^i) - w(u), or nullptr

@@ -117,7 +117,7 @@ extern "C" int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqd
   sp.q = const_cast<double*>(q);  // read only: apply_update = 0
   sp.Np = int(Np);
   StageVol sv = {};
-  sv.kout = dqdt;
+  sv.kout64 = dqdt;
   sv.E = E_elem;
   const int sms = g_sm_count[dev];
   const bool ns = cfg->mu > 0.0;
