@@ -158,6 +158,63 @@ __device__ __forceinline__ void entropy_var_increment_ff(const ff u[5], const ff
   dw[4] = -(beta * xy * iy);
 }
 
+// Relaxation node data in float-float (mixed and ES_FP64X modes): the same quantities
+// as RelaxNode, formed and evaluated on the FP32 pipe; the element sums, the bracket
+// and the Newton/bisection steps stay in FP64.
+struct RelaxNodeF {
+  ff X0, Y0, V2, c;
+};
+
+__device__ __forceinline__ void relax_node_setup_ff(const ff u[5], const ff d[5], const FluxConst<ff>& C, ff c,
+                                                    RelaxNodeF& nd) {
+  const ff rho = u[0];
+  const ff m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+  const ff Pr = C.gm1 * (rho * u[4] - ff_half(m2));
+  const ff inv = ff_rcp(rho * Pr);
+  const ff ir = Pr * inv, ip = rho * rho * inv;
+  const ff v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
+  const ff v2s = v0 * v0 + v1 * v1 + v2 * v2;
+  const ff dv0 = (d[1] - v0 * d[0]) * ir, dv1 = (d[2] - v1 * d[0]) * ir, dv2 = (d[3] - v2 * d[0]) * ir;
+  nd.X0 = d[0] * ir;
+  nd.Y0 = C.gm1 * (d[4] - (v0 * d[1] + v1 * d[2] + v2 * d[3]) + ff_half(v2s * d[0])) * ip;
+  nd.V2 = rho * (dv0 * dv0 + dv1 * dv1 + dv2 * dv2) * ip;
+  nd.c = c;
+}
+
+// the g^3 coefficient (relax_node_cubic) in FP32: it only sets the starting point
+__device__ __forceinline__ float relax_node_cubic_f(const RelaxNodeF& nd, float gam) {
+  const float X = nd.X0.hi, Y = nd.Y0.hi, V = nd.V2.hi;
+  const float y2 = -0.5f * (gam - 1.0f) * V;
+  const float L2 = y2 - 0.5f * Y * Y;
+  const float t = (2.0f * Y * L2 + y2 * Y) * (1.0f / 3.0f) - gam * X * X * X * (1.0f / 6.0f) - X * L2;
+  return t / (gam - 1.0f) - 0.5f * X * V;
+}
+
+// relax_node_eval in float-float (same formulas); false where the state at g is not physical
+__device__ __forceinline__ bool relax_node_eval_ff(const RelaxNodeF& nd, ff g, const FluxConst<ff>& C, ff& D,
+                                                   ff& dD) {
+  const ff one(1.0f, 0.0f);
+  const ff x = g * nd.X0;
+  const ff opx = one + x;
+  const ff K0 = ff_half(g * g * nd.V2);
+  const ff Yb = g * nd.Y0 * opx - C.gm1 * K0;
+  const ff opy_n = opx + Yb;  // (1+y)(1+x)
+  if (!(opx.hi > 0.0f) || !(opy_n.hi > 0.0f)) return false;
+  const ff inv = ff_rcp(opx * opy_n);
+  const ff q = opy_n * inv;       // 1/(1+x)
+  const ff iy = opx * opx * inv;  // 1/(1+y)
+  const ff y = Yb * q;
+  const ff K = K0 * q;
+  const ff Lx = ff_log1pmx(x), Ly = ff_log1pmx(y);
+  const ff l1px = x + Lx, l1py = y + Ly;
+  const ff phi = opx * Lx + x * x;
+  D = (C.gam * phi - Ly - x * l1py) * C.inv_gm1 + K;
+  const ff dK = g * nd.V2 * q * (one - ff_half(x * q));
+  const ff dy = nd.Y0 - C.gm1 * dK;
+  dD = (nd.X0 * (C.gam * l1px - l1py) + dy * (y - x) * iy) * C.inv_gm1 + dK;
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // y = u (+ gamma d when the instance has a pending relaxed update and this is the
 // step's first stage) + dt sum_j a_ij k_j; NPREV stages enter (compile time).
@@ -609,20 +666,50 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
 // Near the root the error after a step s is ~ s^2 r''/(2 r') ~ s^2/g, so a step
 // |s| <= 1e-8 g leaves an error ~1e-16 g: the updated iterate is returned
 // without another evaluation.
-template <int P1>
+template <int P1, typename TF>
 __global__ void k_relax(Params P, StageRelax sr) {
+  // float-float node evaluations in the mixed and ES_FP64X modes (RK mode only: the
+  // u_new entry point always runs the FP64 instantiation)
+  constexpr bool FFE = !std::is_same<TF, double>::value;
   constexpr int Np = P1 * P1 * P1;
   constexpr int R = (Np + 31) / 32;
   const long long N = (long long)P.K * Np;
   const double gam = P.gam;
-  const double inv_gm1 = 1.0 / (gam - 1.0);
+  const double inv_gm1 = P.Cd.inv_gm1;
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
   for (int e = blockIdx.x * warps_per_block + (threadIdx.x >> 5); e < P.K; e += gridDim.x * warps_per_block) {
     const int inst = inst_of(P, e);
     const double J = geom_of(P, inst).J;
     RelaxNode nd[R];
+    RelaxNodeF ndf[R];
     double a_part = 0.0, s_part = 0.0, A_part = 0.0, b_part = 0.0;
+    if constexpr (FFE) {
+      ff a_ff(0.0f, 0.0f);
+      float b_f = 0.0f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int n = lane + 32 * r;
+        ndf[r] = RelaxNodeF{ff(0.0f, 0.0f), ff(0.0f, 0.0f), ff(0.0f, 0.0f), ff(0.0f, 0.0f)};
+        if (n < Np) {
+          const long long g = (long long)e * Np + n;
+          ff u[5], d[5];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            u[v] = ff_from_double(sr.u[v * N + g]);
+            d[v] = ff_from_double(sr.d_in[v * N + g]);
+          }
+          const double c = mass_weight<P1>(P, J, n) * sr.u[g];
+          relax_node_setup_ff(u, d, P.Cff, ff_from_double(c), ndf[r]);
+          s_part += c;
+          const ff XY = ndf[r].X0 - ndf[r].Y0;
+          ff_fma_acc(a_ff, ff_half(ndf[r].c), ndf[r].X0 * ndf[r].X0 + XY * XY * P.Cff.inv_gm1 + ndf[r].V2);
+          b_f = __fmaf_rn(ndf[r].c.hi, relax_node_cubic_f(ndf[r], float(gam)), b_f);
+        }
+      }
+      a_part = double(ff_norm(a_ff));
+      b_part = b_f;
+    } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = lane + 32 * r;
@@ -671,6 +758,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
         }
       }
     }
+    }
     const double a = warp_sum(a_part);
     const double ssum = warp_sum(s_part);
     const double bcub = warp_sum(b_part);
@@ -678,8 +766,8 @@ __global__ void k_relax(Params P, StageRelax sr) {
     if (sr.u_new) A = warp_sum(A_part) - sr.deta[e];
     else A = sr.A[e];
     double gk = __longlong_as_double(0x7ff0000000000000LL);  // +inf: unconstrained
-    const double delta = sqrt(2.0 * a / ssum);
-    if (delta > sr.delta_floor) {
+    // delta_kappa = sqrt(2 a / sum c) > delta_floor, compared without the root and the division
+    if (2.0 * a > sr.delta_floor * sr.delta_floor * ssum) {
       if (!(A < 0.0)) {
         if (lane == 0) atomicOr(sr.status, kStatusNoRoot);
       } else {
@@ -687,13 +775,31 @@ __global__ void k_relax(Params P, StageRelax sr) {
         bool hi_known = false;
         // start: root of the cubic model a g^2 + b g^3 + A g (one Newton step on
         // a + b g + A/g from the quadratic model's root -A/a), off by O(delta^2)
-        double gcur = -A / a;
+        double gcur = -A * fast_rcp(a);
         const double den = a + 2.0 * bcub * gcur;
-        if (den > 0.0) gcur -= bcub * gcur * gcur / den;
+        if (den > 0.0) gcur -= bcub * gcur * gcur * fast_rcp(den);
         gcur = fmin(fmax(gcur, 1e-3), sr.gamma_max);
         for (int it = 0; it < 100; ++it) {
           double sr_ = 0.0, sd_ = 0.0;
           bool ok = true;
+          if constexpr (FFE) {
+            ff sr_f(0.0f, 0.0f), sd_f(0.0f, 0.0f);
+            const ff gf = ff_from_double(gcur);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              ff D, dD;
+              if (ndf[r].c.hi != 0.0f) {
+                if (relax_node_eval_ff(ndf[r], gf, P.Cff, D, dD)) {
+                  ff_fma_acc(sr_f, ndf[r].c, D);
+                  ff_fma_acc(sd_f, ndf[r].c, dD);
+                } else {
+                  ok = false;
+                }
+              }
+            }
+            sr_ = double(ff_norm(sr_f));
+            sd_ = double(ff_norm(sd_f));
+          } else {
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             double D, dD;
@@ -705,6 +811,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
                 ok = false;
               }
             }
+          }
           }
           const bool phys = __all_sync(0xffffffffu, ok);
           const double rv = warp_sum(sr_) + gcur * A;
@@ -719,7 +826,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
             gk = gcur;
             break;
           }
-          const double step = rv / dv;
+          const double step = rv * fast_rcp(dv);
           const double newton = gcur - step;
           // converged: a step this small cannot leave the bracket by more than rounding
           if (phys && dv > 0.0 && fabs(step) <= 1e-8 * gcur) {
@@ -1037,7 +1144,8 @@ void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* a
 
 template <int P1, typename TF>
 void Launcher<P1, TF>::relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid) {
-  k_relax<P1><<<grid, 128, 0, st>>>(P, sr);
+  if (sr.u_new) k_relax<P1, double><<<grid, 128, 0, st>>>(P, sr);
+  else k_relax<P1, TF><<<grid, 128, 0, st>>>(P, sr);
 }
 
 template <int P1, typename TF>
