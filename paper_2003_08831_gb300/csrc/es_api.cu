@@ -154,6 +154,9 @@ void build_params(const es_config& C, Params* out) {
   lgl_tables(C.p, x, w, D);
   for (int i = 0; i < P1; ++i) {
     P.omega[i] = w[i];
+    const ff wf(w[i]);
+    P.omega_ff[0][i] = wf.hi;
+    P.omega_ff[1][i] = wf.lo;
     for (int j = 0; j < P1; ++j) {
       P.D[i * P1 + j] = D[i * P1 + j];
       P.D2[i * P1 + j] = (i == j) ? 0.0 : 2.0 * D[i * P1 + j];

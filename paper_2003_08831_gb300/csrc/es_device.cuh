@@ -51,6 +51,7 @@ struct Params {
   float Dff[2][kMaxP1 * kMaxP1];   // D and 2 D split into float-float (hi, lo)
   float D2ff[2][kMaxP1 * kMaxP1];
   double omega[kMaxP1];        // LGL weights
+  float omega_ff[2][kMaxP1];   // LGL weights split into float-float (hi, lo)
   double inv_omega_end;        // 1/omega_0 = 1/omega_p
   double gam;                  // ratio of specific heats
   double mu, kappa_heat, R;    // viscosity, heat conductivity mu c_p / Pr, gas constant
@@ -123,6 +124,23 @@ template <> struct Tab<ff> {
 __device__ __forceinline__ void fma_acc(double& acc, double a, double b) { acc = fma(a, b, acc); }
 __device__ __forceinline__ void fma_acc(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
 __device__ __forceinline__ void fma_acc(ff& acc, ff a, ff b) { ff_fma_acc(acc, a, b); }
+
+// a double in the flux precision without FP64 instructions (float: the split rounded once)
+template <typename T> __device__ __forceinline__ T tf_from_double(double x);
+template <> __device__ __forceinline__ double tf_from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ ff tf_from_double<ff>(double x) { return ff_from_double(x); }
+template <> __device__ __forceinline__ float tf_from_double<float>(double x) {
+  const ff s = ff_from_double(x);
+  return __fadd_rn(s.hi, s.lo);
+}
+
+// omega_i omega_j omega_k of node n in float-float
+template <int P1>
+__device__ __forceinline__ ff mass_weight_ff(const Params& P, int n) {
+  const int i = n % P1, j = (n / P1) % P1, k = n / (P1 * P1);
+  return ff(P.omega_ff[0][i], P.omega_ff[1][i]) * ff(P.omega_ff[0][j], P.omega_ff[1][j]) *
+         ff(P.omega_ff[0][k], P.omega_ff[1][k]);
+}
 
 // ---------------------------------------------------------------------------
 // Parameter-vector state used by the two-point flux: z = sqrt(rho/p) (1, v, p).

@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
   const int nel = min(EPB, P.K - e0);
   const int nn = nel * Np;
   const FluxConst<TF> C = flux_const<TF>(P);
-  const TF iw = TF(P.inv_omega_end);
+  const TF iw = tf_from_double<TF>(P.inv_omega_end);
 
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
 #pragma unroll
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
       const int el = l / P2, ab = l % P2;
       const int a = ab % P1, b = ab / P1;
       const int e = e0 + el;
-      const TF met = TF(geom_of(P, inst_of(P, e)).metric[m]);
+      const TF met = tf_from_double<TF>(geom_of(P, inst_of(P, e)).metric[m]);
       Zstate<TF> z[P1];
 #pragma unroll
       for (int i = 0; i < P1; ++i) {
@@ -556,8 +556,8 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
     const long long g = (long long)e0 * Np + t;
     const int n = t % Np;
     const InstGeom& G = geom_of(P, inst_of(P, e0 + t / Np));
-    const double Pn = mass_weight<P1>(P, G.J, n);
     if constexpr (std::is_same<TF, double>::value) {
+      const double Pn = mass_weight<P1>(P, G.J, n);
       double k[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) k[v] = acc[v * EPB * Np + t];
@@ -599,15 +599,16 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
 #pragma unroll
       for (int v = 0; v < 5; ++v) kt[v] = acc[v * EPB * Np + t];
       if (sv.d_out) {
-        const double dt = G.dt;
-        const ff cs = ff_from_double(sv.dcoef_self * dt);
+        // d = dt (b_i k_i + sum_j b_j k_j): coefficients and dt split on the integer pipe
+        const ff dtf = ff_from_double(G.dt);
+        const ff cs = ff_from_double(sv.dcoef_self);
         ff cj[4];
-        for (int j = 0; j < sv.nd; ++j) cj[j] = ff_from_double(sv.dcoef[j] * dt);
+        for (int j = 0; j < sv.nd; ++j) cj[j] = ff_from_double(sv.dcoef[j]);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           ff dv = cs * to_ff(kt[v]);
           for (int j = 0; j < sv.nd; ++j) ff_fma_acc(dv, cj[j], to_ff(static_cast<const TF*>(sv.dk[j])[v * N + g]));
-          sv.d_out[v * N + g] = double(ff_norm(dv));
+          sv.d_out[v * N + g] = double(ff_norm(dv) * dtf);
         }
       } else if (sv.kout64) {
 #pragma unroll
@@ -626,13 +627,14 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
         double sum = 0.0;
 #pragma unroll
         for (int v = 0; v < 5; ++v) sum += double(w[v]) * double(kt[v]);
-        red[t] = Pn * sum;
+        red[t] = mass_weight<P1>(P, G.J, n) * sum;
       }
       if (wantA) {
+        // omega_i omega_j omega_k w-increment . k in float-float; J dt enter per element
         ff sum(0.0f, 0.0f);
 #pragma unroll
         for (int v = 0; v < 5; ++v) ff_fma_acc(sum, ff_from_double(sv.dw[v * N + g]), to_ff(kt[v]));
-        red[EPB * Np + t] = Pn * G.dt * double(ff_norm(sum));
+        reinterpret_cast<ff*>(red)[EPB * Np + t] = mass_weight_ff<P1>(P, n) * ff_norm(sum);
       }
     }
   }
@@ -644,10 +646,22 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
     double sE = 0.0, sA = 0.0;
     for (int n = lane; n < Np; n += 32) {
       if (wantE) sE += red[el * Np + n];
-      if (wantA) sA += red[EPB * Np + el * Np + n];
+      if constexpr (std::is_same<TF, double>::value) {
+        if (wantA) sA += red[EPB * Np + el * Np + n];
+      }
     }
     sE = warp_sum(sE);
-    sA = warp_sum(sA);
+    if constexpr (std::is_same<TF, double>::value) {
+      sA = warp_sum(sA);
+    } else if (wantA) {
+      ff s(0.0f, 0.0f);
+      for (int n = lane; n < Np; n += 32) s = s + reinterpret_cast<const ff*>(red)[EPB * Np + el * Np + n];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        s = s + ff(__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o));
+      const InstGeom& G = geom_of(P, inst_of(P, e0 + el));
+      sA = double(s) * (G.J * G.dt);
+    }
     if (lane == 0) {
       const int e = e0 + el;
       if (wantE) sv.E[e] = sE;
@@ -666,11 +680,8 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
 // Near the root the error after a step s is ~ s^2 r''/(2 r') ~ s^2/g, so a step
 // |s| <= 1e-8 g leaves an error ~1e-16 g: the updated iterate is returned
 // without another evaluation.
-template <int P1, typename TF>
+template <int P1>
 __global__ void k_relax(Params P, StageRelax sr) {
-  // float-float node evaluations in the mixed and ES_FP64X modes (RK mode only: the
-  // u_new entry point always runs the FP64 instantiation)
-  constexpr bool FFE = !std::is_same<TF, double>::value;
   constexpr int Np = P1 * P1 * P1;
   constexpr int R = (Np + 31) / 32;
   const long long N = (long long)P.K * Np;
@@ -682,34 +693,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
     const int inst = inst_of(P, e);
     const double J = geom_of(P, inst).J;
     RelaxNode nd[R];
-    RelaxNodeF ndf[R];
     double a_part = 0.0, s_part = 0.0, A_part = 0.0, b_part = 0.0;
-    if constexpr (FFE) {
-      ff a_ff(0.0f, 0.0f);
-      float b_f = 0.0f;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int n = lane + 32 * r;
-        ndf[r] = RelaxNodeF{ff(0.0f, 0.0f), ff(0.0f, 0.0f), ff(0.0f, 0.0f), ff(0.0f, 0.0f)};
-        if (n < Np) {
-          const long long g = (long long)e * Np + n;
-          ff u[5], d[5];
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            u[v] = ff_from_double(sr.u[v * N + g]);
-            d[v] = ff_from_double(sr.d_in[v * N + g]);
-          }
-          const double c = mass_weight<P1>(P, J, n) * sr.u[g];
-          relax_node_setup_ff(u, d, P.Cff, ff_from_double(c), ndf[r]);
-          s_part += c;
-          const ff XY = ndf[r].X0 - ndf[r].Y0;
-          ff_fma_acc(a_ff, ff_half(ndf[r].c), ndf[r].X0 * ndf[r].X0 + XY * XY * P.Cff.inv_gm1 + ndf[r].V2);
-          b_f = __fmaf_rn(ndf[r].c.hi, relax_node_cubic_f(ndf[r], float(gam)), b_f);
-        }
-      }
-      a_part = double(ff_norm(a_ff));
-      b_part = b_f;
-    } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = lane + 32 * r;
@@ -758,7 +742,6 @@ __global__ void k_relax(Params P, StageRelax sr) {
         }
       }
     }
-    }
     const double a = warp_sum(a_part);
     const double ssum = warp_sum(s_part);
     const double bcub = warp_sum(b_part);
@@ -782,24 +765,6 @@ __global__ void k_relax(Params P, StageRelax sr) {
         for (int it = 0; it < 100; ++it) {
           double sr_ = 0.0, sd_ = 0.0;
           bool ok = true;
-          if constexpr (FFE) {
-            ff sr_f(0.0f, 0.0f), sd_f(0.0f, 0.0f);
-            const ff gf = ff_from_double(gcur);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-              ff D, dD;
-              if (ndf[r].c.hi != 0.0f) {
-                if (relax_node_eval_ff(ndf[r], gf, P.Cff, D, dD)) {
-                  ff_fma_acc(sr_f, ndf[r].c, D);
-                  ff_fma_acc(sd_f, ndf[r].c, dD);
-                } else {
-                  ok = false;
-                }
-              }
-            }
-            sr_ = double(ff_norm(sr_f));
-            sd_ = double(ff_norm(sd_f));
-          } else {
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             double D, dD;
@@ -811,7 +776,6 @@ __global__ void k_relax(Params P, StageRelax sr) {
                 ok = false;
               }
             }
-          }
           }
           const bool phys = __all_sync(0xffffffffu, ok);
           const double rv = warp_sum(sr_) + gcur * A;
@@ -842,6 +806,132 @@ __global__ void k_relax(Params P, StageRelax sr) {
           else if (!hi_known) gcur = (gcur >= sr.gamma_max) ? sr.gamma_max : fmin(2.0 * gcur, sr.gamma_max);
           else gcur = 0.5 * (lo + hi);
           if (!hi_known && lo >= sr.gamma_max) {  // r(gamma_max) <= 0: capped
+            gk = sr.gamma_max;
+            break;
+          }
+        }
+      }
+    }
+    if (lane == 0) {
+      sr.gamma_elem[e] = gk;
+      atomic_min_positive(sr.gmin_bits + inst, gk);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_relax in float-float for the mixed and ES_FP64X modes: node data, element sums,
+// bracket and Newton steps on the FP32 pipe (es_ff.cuh; ~2^-47 relative), the root
+// joined to FP64 once per element.  Same rules as k_relax; the bracket-width stop is
+// 2^-44 max(1, gamma) (the float-float resolution) instead of 4 * 2^-52.
+__device__ __forceinline__ ff warp_sum_ff(ff v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = v + ff(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ ff ff_min(ff x, ff y) { return y < x ? y : x; }
+__device__ __forceinline__ ff ff_max(ff x, ff y) { return x < y ? y : x; }
+
+template <int P1>
+__global__ void k_relax_ff(Params P, StageRelax sr) {
+  constexpr int Np = P1 * P1 * P1;
+  constexpr int R = (Np + 31) / 32;
+  const long long N = (long long)P.K * Np;
+  const FluxConst<ff>& C = P.Cff;
+  const int lane = threadIdx.x & 31;
+  const int warps_per_block = blockDim.x >> 5;
+  const float floor2 = float(sr.delta_floor * sr.delta_floor);
+  const ff gmax = ff_from_double(sr.gamma_max);
+  const ff zero(0.0f, 0.0f);
+  for (int e = blockIdx.x * warps_per_block + (threadIdx.x >> 5); e < P.K; e += gridDim.x * warps_per_block) {
+    const int inst = inst_of(P, e);
+    const ff J = ff_from_double(geom_of(P, inst).J);
+    RelaxNodeF nd[R];
+    ff a_p = zero, s_p = zero;
+    float b_p = 0.0f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = lane + 32 * r;
+      nd[r] = RelaxNodeF{zero, zero, zero, zero};
+      if (n < Np) {
+        const long long g = (long long)e * Np + n;
+        ff u[5], d[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          u[v] = ff_from_double(sr.u[v * N + g]);
+          d[v] = ff_from_double(sr.d_in[v * N + g]);
+        }
+        relax_node_setup_ff(u, d, C, mass_weight_ff<P1>(P, n) * J * u[0], nd[r]);
+        s_p = s_p + nd[r].c;
+        const ff XY = nd[r].X0 - nd[r].Y0;
+        ff_fma_acc(a_p, ff_half(nd[r].c), nd[r].X0 * nd[r].X0 + XY * XY * C.inv_gm1 + nd[r].V2);
+        b_p = __fmaf_rn(nd[r].c.hi, relax_node_cubic_f(nd[r], C.gam.hi), b_p);
+      }
+    }
+    const ff a = warp_sum_ff(ff_norm(a_p));
+    const ff ssum = warp_sum_ff(s_p);
+    const float bcub = warp_sum_f(b_p);
+    const ff A = ff_from_double(sr.A[e]);
+    double gk = __longlong_as_double(0x7ff0000000000000LL);  // +inf: unconstrained
+    if (2.0f * a.hi > floor2 * ssum.hi) {                      // delta_kappa > delta_floor
+      if (!(A.hi < 0.0f)) {
+        if (lane == 0) atomicOr(sr.status, kStatusNoRoot);
+      } else {
+        ff lo = zero, hi = gmax;
+        bool hi_known = false;
+        ff gcur = -(A * ff_rcp(a));
+        const ff bf(bcub, 0.0f);
+        const ff den = a + ff_twice(bf * gcur);
+        if (den.hi > 0.0f) gcur = gcur - bf * gcur * gcur * ff_rcp(den);
+        gcur = ff_min(ff_max(gcur, ff(1e-3f, 0.0f)), gmax);
+        for (int it = 0; it < 100; ++it) {
+          ff sr_f = zero, sd_f = zero;
+          bool ok = true;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            ff D, dD;
+            if (nd[r].c.hi != 0.0f) {
+              if (relax_node_eval_ff(nd[r], gcur, C, D, dD)) {
+                ff_fma_acc(sr_f, nd[r].c, D);
+                ff_fma_acc(sd_f, nd[r].c, dD);
+              } else {
+                ok = false;
+              }
+            }
+          }
+          const bool phys = __all_sync(0xffffffffu, ok);
+          const ff rv = warp_sum_ff(ff_norm(sr_f)) + gcur * A;
+          const ff dv = warp_sum_ff(ff_norm(sd_f)) + A;
+          if (!phys || rv.hi > 0.0f) {
+            hi = gcur;
+            hi_known = true;
+          } else {
+            lo = gcur;
+          }
+          if (phys && rv.hi == 0.0f) {
+            gk = double(gcur);
+            break;
+          }
+          const ff step = rv * ff_rcp(dv);
+          const ff newton = gcur - step;
+          if (phys && dv.hi > 0.0f && fabsf(step.hi) <= 1e-8f * gcur.hi) {
+            gk = double(ff_min(ff_max(newton, lo), hi));
+            break;
+          }
+          const bool nok = phys && dv.hi > 0.0f && isfinite(newton.hi) && lo < newton && newton < hi;
+          if ((hi - lo).hi <= 5.684341886080802e-14f * fmaxf(1.0f, gcur.hi)) {  // 2^-44
+            gk = double(lo);
+            break;
+          }
+          if (nok) gcur = newton;
+          else if (!hi_known) gcur = (gmax < gcur || !(gcur < gmax)) ? gmax : ff_min(ff_twice(gcur), gmax);
+          else gcur = ff_half(lo + hi);
+          if (!hi_known && !(lo < gmax)) {  // r(gamma_max) <= 0: capped
             gk = sr.gamma_max;
             break;
           }
@@ -1144,8 +1234,9 @@ void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* a
 
 template <int P1, typename TF>
 void Launcher<P1, TF>::relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid) {
-  if (sr.u_new) k_relax<P1, double><<<grid, 128, 0, st>>>(P, sr);
-  else k_relax<P1, TF><<<grid, 128, 0, st>>>(P, sr);
+  // the u_new entry point (es_relax_step) and the FP64 mode solve in FP64
+  if (sr.u_new || std::is_same<TF, double>::value) k_relax<P1><<<grid, 128, 0, st>>>(P, sr);
+  else k_relax_ff<P1><<<grid, 128, 0, st>>>(P, sr);
 }
 
 template <int P1, typename TF>
