@@ -72,6 +72,30 @@ def volume_flops_per_element(p, ns=False, with_A=False):
     return f
 
 
+# Algorithmic work of the other kernels per unit, counted from their FP64 sources the same
+# way (FMA = 2; reciprocal, rsqrt, log each 1; the series logarithms by their terms):
+# k_face per face node: Ismail--Roe flux 56 + Rusanov dissipation 55 (two conserved
+#   states from z 2 x 19, lambda 2, 5 jump terms 15);
+# k_prep per node: parameter vector 22 + 10 per earlier stage combined (+10 for the pending
+#   update in the first stage); entropy-variable increments 131 in stages 2 and 3;
+# k_relax per node and step: setup 85 (primitive state 35, X0 Y0 V2 25, a and the cubic
+#   coefficient 25) + 75 per Bregman evaluation (one for a smooth step from the cubic start).
+FACE_FLOPS_PER_FACE_NODE = 56 + 55
+PREP_FLOPS_Z, PREP_FLOPS_PER_STAGE, PREP_FLOPS_PENDING, PREP_FLOPS_DW = 22, 10, 10, 131
+RELAX_FLOPS_SETUP, RELAX_FLOPS_EVAL = 85, 75
+
+
+def kernel_flops(p, n_el, stages=3):
+    """Algorithmic FP64 flops per launch (averaged over the step's launches) of each kernel."""
+    P1 = p + 1
+    nodes = n_el * P1 ** 3
+    prep = nodes * (PREP_FLOPS_Z * stages + PREP_FLOPS_PENDING
+                    + sum(PREP_FLOPS_PER_STAGE * i + (PREP_FLOPS_DW if i > 0 else 0) for i in range(stages))) / stages
+    face = 3 * n_el * P1 * P1 * FACE_FLOPS_PER_FACE_NODE
+    relax = nodes * (RELAX_FLOPS_SETUP + RELAX_FLOPS_EVAL)
+    return {"prep": prep, "face": face, "relax": relax}
+
+
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_volume launch of the
 # default workload, from the ncu capture summarised in profiles/ (stage 3 of a step, FP64).
 # It is reported only while the kernel sources hash to the value the capture was taken with.
@@ -296,6 +320,22 @@ def measure_batch(precision, steps, warmup, count=256):
     return out
 
 
+def kernel_roofline(p, n_el, wl, prof, peak, vol_flops):
+    """Per kernel kind: algorithmic flops per launch / average event-timed launch, as a
+    fraction of the ALU peak (FP64 workloads; other precisions report null)."""
+    if wl["precision"] != 0 or wl["mu"] > 0:
+        return None
+    fl = kernel_flops(p, n_el)
+    fl["volume"] = vol_flops
+    out = {}
+    for k, f in fl.items():
+        ms, n = prof.get(k, (0.0, 0))
+        if n:
+            a = f / (ms / n * 1e-3) / 1e12
+            out[k] = {"flops_per_launch": f, "avg_launch_ms": ms / n, "achieved_tflops": a, "frac": a / peak}
+    return out
+
+
 def kernel_profile(res, steps):
     """Second pass with per-launch CUDA events: time per kernel kind."""
     import torch
@@ -471,6 +511,7 @@ def run_full(args, rank, world, local_rank):
                                        "2 DFMA/clk" if wl["precision"] == 0 else "128 FFMA/clk"),
                      "flops_per_launch": fl, "avg_launch_ms": avg_ms},
         "kernel_share": {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1] > 0},
+        "kernel_roofline": kernel_roofline(p, K, wl, prof, peak, fl),
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu:
