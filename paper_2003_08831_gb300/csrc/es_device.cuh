@@ -48,8 +48,8 @@ struct FluxConst {
 struct Params {
   double D[kMaxP1 * kMaxP1];   // SBP derivative on [-1, 1], row-major
   double D2[kMaxP1 * kMaxP1];  // 2 D_ij (i != j), 0 on the diagonal
-  float Dff[2][kMaxP1 * kMaxP1];   // D and 2 D split into float-float (hi, lo)
-  float D2ff[2][kMaxP1 * kMaxP1];
+  float Dff[2][kMaxP1 * kMaxP1];   // D and 2 D split into float-float (hi, lo); hi is
+  float D2ff[2][kMaxP1 * kMaxP1];  // the FP32 table (round to nearest) of the mixed mode
   double omega[kMaxP1];        // LGL weights
   float omega_ff[2][kMaxP1];   // LGL weights split into float-float (hi, lo)
   double inv_omega_end;        // 1/omega_0 = 1/omega_p
@@ -111,8 +111,8 @@ template <> struct Tab<double> {
   static __device__ __forceinline__ double D2(const Params& P, int i) { return P.D2[i]; }
 };
 template <> struct Tab<float> {
-  static __device__ __forceinline__ float D(const Params& P, int i) { return float(P.D[i]); }
-  static __device__ __forceinline__ float D2(const Params& P, int i) { return float(P.D2[i]); }
+  static __device__ __forceinline__ float D(const Params& P, int i) { return P.Dff[0][i]; }
+  static __device__ __forceinline__ float D2(const Params& P, int i) { return P.D2ff[0][i]; }
 };
 template <> struct Tab<ff> {
   static __device__ __forceinline__ ff D(const Params& P, int i) { return ff(P.Dff[0][i], P.Dff[1][i]); }
@@ -160,18 +160,17 @@ template <typename T> struct LogMeanConst;
 template <> struct LogMeanConst<double> { static constexpr double eps = 1.0e-4; };
 template <> struct LogMeanConst<float> { static constexpr float eps = 1.0e-2f; };
 
-// 1/x for FP64 without the IEEE division sequence: the hardware approximation
-// (PTX rcp.approx.ftz.f64) refined by two Newton--Raphson steps r <- r + r (1 - x r),
-// each doubling the number of correct bits.  x must be a normal positive or
-// negative number (subnormals flush to zero); the result is within a few units
-// in the last place of 1/x, not correctly rounded.
+// 1/x for FP64 without the IEEE division sequence: the hardware approximation r
+// (PTX rcp.approx.ftz.f64) refined by one third-order step of the series
+// 1/x = r/(1 - e) = r (1 + e + e^2 + ...), e = 1 - x r (three fmas; the truncation
+// r e^3 is below 2^-60 for an approximation good to 2^-20).  x must be a normal
+// positive or negative number (subnormals flush to zero); the result is within one
+// unit in the last place of 1/x, not correctly rounded.
 __device__ __forceinline__ double fast_rcp(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 __device__ __forceinline__ float fast_rcp(float x) { return 1.0f / x; }
 __device__ __forceinline__ ff fast_rcp(ff x) { return ff_rcp(x); }

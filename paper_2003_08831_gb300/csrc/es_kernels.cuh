@@ -158,6 +158,33 @@ __device__ __forceinline__ void entropy_var_increment_ff(const ff u[5], const ff
   dw[4] = -(beta * xy * iy);
 }
 
+// Lanes per element in the relaxation kernels: a group of SUB lanes solves one element,
+// so for Np <= 64 two or four elements share a warp and the per-element scalar work
+// (reductions, bracket and Newton logic, executed by every lane of the group) is paid
+// once per 16 or 8 lanes instead of once per warp.
+template <int P1>
+struct RelaxGroup {
+  static constexpr int Np = P1 * P1 * P1;
+  static constexpr int SUB = Np <= 32 ? 8 : (Np <= 64 ? 16 : 32);
+  static constexpr int R = (Np + SUB - 1) / SUB;  // nodes per lane
+  static constexpr int EPW = 32 / SUB;            // elements per warp
+  static __device__ __forceinline__ unsigned mask(int lane) {
+    return SUB == 32 ? 0xffffffffu : (((1u << SUB) - 1u) << (lane / SUB * SUB));
+  }
+};
+template <int SUB>
+__device__ __forceinline__ double group_sum(double v, unsigned mask) {
+#pragma unroll
+  for (int o = SUB / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+template <int SUB>
+__device__ __forceinline__ float group_sum_f(float v, unsigned mask) {
+#pragma unroll
+  for (int o = SUB / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
 // Relaxation node data in float-float (mixed and ES_FP64X modes): the same quantities
 // as RelaxNode, formed and evaluated on the FP32 pipe; the element sums, the bracket
 // and the Newton/bisection steps stay in FP64.
@@ -650,7 +677,7 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
         if (wantA) sA += red[EPB * Np + el * Np + n];
       }
     }
-    sE = warp_sum(sE);
+    if (wantE) sE = warp_sum(sE);
     if constexpr (std::is_same<TF, double>::value) {
       sA = warp_sum(sA);
     } else if (wantA) {
@@ -682,21 +709,24 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
 // without another evaluation.
 template <int P1>
 __global__ void k_relax(Params P, StageRelax sr) {
-  constexpr int Np = P1 * P1 * P1;
-  constexpr int R = (Np + 31) / 32;
+  using RG = RelaxGroup<P1>;
+  constexpr int Np = RG::Np, R = RG::R, SUB = RG::SUB;
   const long long N = (long long)P.K * Np;
   const double gam = P.gam;
   const double inv_gm1 = P.Cd.inv_gm1;
   const int lane = threadIdx.x & 31;
+  const int sl = lane % SUB;                  // lane within the element's group
+  const unsigned gmask = RG::mask(lane);
   const int warps_per_block = blockDim.x >> 5;
-  for (int e = blockIdx.x * warps_per_block + (threadIdx.x >> 5); e < P.K; e += gridDim.x * warps_per_block) {
+  for (int e = (blockIdx.x * warps_per_block + (threadIdx.x >> 5)) * RG::EPW + lane / SUB; e < P.K;
+       e += gridDim.x * warps_per_block * RG::EPW) {
     const int inst = inst_of(P, e);
     const double J = geom_of(P, inst).J;
     RelaxNode nd[R];
     double a_part = 0.0, s_part = 0.0, A_part = 0.0, b_part = 0.0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int n = lane + 32 * r;
+      const int n = sl + SUB * r;
       nd[r].X0 = nd[r].Y0 = nd[r].V2 = nd[r].c = 0.0;
       if (n < Np) {
         const long long g = (long long)e * Np + n;
@@ -742,17 +772,18 @@ __global__ void k_relax(Params P, StageRelax sr) {
         }
       }
     }
-    const double a = warp_sum(a_part);
-    const double ssum = warp_sum(s_part);
-    const double bcub = warp_sum(b_part);
+    const double a = group_sum<SUB>(a_part, gmask);
+    const double ssum = group_sum<SUB>(s_part, gmask);
+    // the cubic coefficient only moves the starting point: an FP32 sum
+    const double bcub = group_sum_f<SUB>(float(b_part), gmask);
     double A;
-    if (sr.u_new) A = warp_sum(A_part) - sr.deta[e];
+    if (sr.u_new) A = group_sum<SUB>(A_part, gmask) - sr.deta[e];
     else A = sr.A[e];
     double gk = __longlong_as_double(0x7ff0000000000000LL);  // +inf: unconstrained
     // delta_kappa = sqrt(2 a / sum c) > delta_floor, compared without the root and the division
     if (2.0 * a > sr.delta_floor * sr.delta_floor * ssum) {
       if (!(A < 0.0)) {
-        if (lane == 0) atomicOr(sr.status, kStatusNoRoot);
+        if (sl == 0) atomicOr(sr.status, kStatusNoRoot);
       } else {
         double lo = 0.0, hi = sr.gamma_max;
         bool hi_known = false;
@@ -777,9 +808,9 @@ __global__ void k_relax(Params P, StageRelax sr) {
               }
             }
           }
-          const bool phys = __all_sync(0xffffffffu, ok);
-          const double rv = warp_sum(sr_) + gcur * A;
-          const double dv = warp_sum(sd_) + A;
+          const bool phys = __all_sync(gmask, ok);
+          const double rv = group_sum<SUB>(sr_, gmask) + gcur * A;
+          const double dv = group_sum<SUB>(sd_, gmask) + A;
           if (!phys || rv > 0.0) {
             hi = gcur;
             hi_known = true;
@@ -812,7 +843,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
         }
       }
     }
-    if (lane == 0) {
+    if (sl == 0) {
       sr.gamma_elem[e] = gk;
       atomic_min_positive(sr.gmin_bits + inst, gk);
     }
@@ -824,14 +855,11 @@ __global__ void k_relax(Params P, StageRelax sr) {
 // bracket and Newton steps on the FP32 pipe (es_ff.cuh; ~2^-47 relative), the root
 // joined to FP64 once per element.  Same rules as k_relax; the bracket-width stop is
 // 2^-44 max(1, gamma) (the float-float resolution) instead of 4 * 2^-52.
-__device__ __forceinline__ ff warp_sum_ff(ff v) {
+// float-float / FP32 sums over a lane group (butterfly within the group's lanes)
+template <int SUB>
+__device__ __forceinline__ ff group_sum_ff(ff v, unsigned mask) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = v + ff(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
-  return v;
-}
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = SUB / 2; o > 0; o >>= 1) v = v + ff(__shfl_xor_sync(mask, v.hi, o), __shfl_xor_sync(mask, v.lo, o));
   return v;
 }
 __device__ __forceinline__ ff ff_min(ff x, ff y) { return y < x ? y : x; }
@@ -839,16 +867,19 @@ __device__ __forceinline__ ff ff_max(ff x, ff y) { return x < y ? y : x; }
 
 template <int P1>
 __global__ void k_relax_ff(Params P, StageRelax sr) {
-  constexpr int Np = P1 * P1 * P1;
-  constexpr int R = (Np + 31) / 32;
+  using RG = RelaxGroup<P1>;
+  constexpr int Np = RG::Np, R = RG::R, SUB = RG::SUB;
   const long long N = (long long)P.K * Np;
   const FluxConst<ff>& C = P.Cff;
   const int lane = threadIdx.x & 31;
+  const int sl = lane % SUB;
+  const unsigned gmask = RG::mask(lane);
   const int warps_per_block = blockDim.x >> 5;
   const float floor2 = float(sr.delta_floor * sr.delta_floor);
   const ff gmax = ff_from_double(sr.gamma_max);
   const ff zero(0.0f, 0.0f);
-  for (int e = blockIdx.x * warps_per_block + (threadIdx.x >> 5); e < P.K; e += gridDim.x * warps_per_block) {
+  for (int e = (blockIdx.x * warps_per_block + (threadIdx.x >> 5)) * RG::EPW + lane / SUB; e < P.K;
+       e += gridDim.x * warps_per_block * RG::EPW) {
     const int inst = inst_of(P, e);
     const ff J = ff_from_double(geom_of(P, inst).J);
     RelaxNodeF nd[R];
@@ -856,7 +887,7 @@ __global__ void k_relax_ff(Params P, StageRelax sr) {
     float b_p = 0.0f;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int n = lane + 32 * r;
+      const int n = sl + SUB * r;
       nd[r] = RelaxNodeF{zero, zero, zero, zero};
       if (n < Np) {
         const long long g = (long long)e * Np + n;
@@ -873,14 +904,14 @@ __global__ void k_relax_ff(Params P, StageRelax sr) {
         b_p = __fmaf_rn(nd[r].c.hi, relax_node_cubic_f(nd[r], C.gam.hi), b_p);
       }
     }
-    const ff a = warp_sum_ff(ff_norm(a_p));
-    const ff ssum = warp_sum_ff(s_p);
-    const float bcub = warp_sum_f(b_p);
+    const ff a = group_sum_ff<SUB>(ff_norm(a_p), gmask);
+    const float ssum = group_sum_f<SUB>(s_p.hi, gmask);
+    const float bcub = group_sum_f<SUB>(b_p, gmask);
     const ff A = ff_from_double(sr.A[e]);
     double gk = __longlong_as_double(0x7ff0000000000000LL);  // +inf: unconstrained
-    if (2.0f * a.hi > floor2 * ssum.hi) {                      // delta_kappa > delta_floor
+    if (2.0f * a.hi > floor2 * ssum) {                         // delta_kappa > delta_floor
       if (!(A.hi < 0.0f)) {
-        if (lane == 0) atomicOr(sr.status, kStatusNoRoot);
+        if (sl == 0) atomicOr(sr.status, kStatusNoRoot);
       } else {
         ff lo = zero, hi = gmax;
         bool hi_known = false;
@@ -904,9 +935,9 @@ __global__ void k_relax_ff(Params P, StageRelax sr) {
               }
             }
           }
-          const bool phys = __all_sync(0xffffffffu, ok);
-          const ff rv = warp_sum_ff(ff_norm(sr_f)) + gcur * A;
-          const ff dv = warp_sum_ff(ff_norm(sd_f)) + A;
+          const bool phys = __all_sync(gmask, ok);
+          const ff rv = group_sum_ff<SUB>(ff_norm(sr_f), gmask) + gcur * A;
+          const ff dv = group_sum_ff<SUB>(ff_norm(sd_f), gmask) + A;
           if (!phys || rv.hi > 0.0f) {
             hi = gcur;
             hi_known = true;
@@ -938,7 +969,7 @@ __global__ void k_relax_ff(Params P, StageRelax sr) {
         }
       }
     }
-    if (lane == 0) {
+    if (sl == 0) {
       sr.gamma_elem[e] = gk;
       atomic_min_positive(sr.gmin_bits + inst, gk);
     }
@@ -1234,9 +1265,12 @@ void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* a
 
 template <int P1, typename TF>
 void Launcher<P1, TF>::relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid) {
-  // the u_new entry point (es_relax_step) and the FP64 mode solve in FP64
-  if (sr.u_new || std::is_same<TF, double>::value) k_relax<P1><<<grid, 128, 0, st>>>(P, sr);
-  else k_relax_ff<P1><<<grid, 128, 0, st>>>(P, sr);
+  // the u_new entry point (es_relax_step) and the FP64 mode solve in FP64; 4 warps per
+  // block, RelaxGroup<P1>::EPW elements per warp
+  const int need = (P.K + 4 * RelaxGroup<P1>::EPW - 1) / (4 * RelaxGroup<P1>::EPW);
+  const int g = grid < need ? grid : need;
+  if (sr.u_new || std::is_same<TF, double>::value) k_relax<P1><<<g, 128, 0, st>>>(P, sr);
+  else k_relax_ff<P1><<<g, 128, 0, st>>>(P, sr);
 }
 
 template <int P1, typename TF>

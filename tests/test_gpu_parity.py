@@ -456,7 +456,7 @@ def test_local_gamma_variation_x6():
 
 
 def test_reciprocal_matches_ieee_division():
-    """The kernels' FP64 reciprocal (hardware approximation + two Newton steps) against
+    """The kernels' FP64 reciprocal (hardware approximation + one third-order step) against
     IEEE 1/x over random mantissas and exponents 2^-300 .. 2^300: within one ulp."""
     import torch
     from paper_2003_08831_gb300 import _binding as B
