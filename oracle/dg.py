@@ -17,7 +17,13 @@ dissipation and viscous details to its references; the readings taken here:
   toward the face average of w], viscous flux F^V_m(q, theta), divergence
   (2/h_m)[D F^V_m + lifting toward the face average of F^V_m].  diss^V = 0.
 * Mesh: n_x x n_y x n_z elements of size h_x x h_y x h_z, periodic in every
-  direction; metric 2/h_m per direction, Jacobian h_x h_y h_z / 8.
+  direction unless a Dirichlet-penalty boundary is given for it; metric 2/h_m per
+  direction, Jacobian h_x h_y h_z / 8.
+* Dirichlet-penalty boundaries (Section 4.1.2 penalises the solution against the
+  analytic one; the form is not printed).  Reading: at a boundary face the exterior
+  state is the prescribed state q_b(t); the inviscid SAT uses the interface flux
+  f_num(q, q_b) (left boundary: f_num(q_b, q)); the BR1 gradient lifts toward
+  (w + w(q_b))/2; the viscous boundary flux is the interior one (no viscous penalty).
 
 Array layout: U has shape (5, nz, ny, nx, P1, P1, P1) with node axes (k, j, i)
 running in (z, y, x).  Flattened in C order this is the SoA layout
@@ -42,7 +48,10 @@ class Physics:
 
 
 class Mesh:
-    def __init__(self, p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    def __init__(self, p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=None):
+        """bc: {direction m: (left(t), right(t))} prescribed exterior states (5,) at the
+        faces x_m = lo_m and x_m = hi_m; directions not listed are periodic."""
+        self.bc = dict(bc or {})
         self.p = int(p)
         self.P1 = self.p + 1
         self.n = tuple(int(a) for a in n)             # (nx, ny, nz)
@@ -91,6 +100,32 @@ class Mesh:
         return np.asarray(q, dtype=np.float64).reshape(self.shape)
 
 
+def _next_trace(mesh, A_left, m, eax, t, fn=None):
+    """Trace of the +x_m neighbour at each element's +x_m face: its -x_m face values,
+    or the prescribed right boundary state (through fn) on the last element."""
+    out = np.roll(A_left, -1, axis=eax)
+    if m in mesh.bc:
+        qb = np.asarray(mesh.bc[m][1](t), dtype=np.float64)
+        val = qb if fn is None else fn(qb)
+        idx = [slice(None)] * out.ndim
+        idx[eax] = -1
+        out[tuple(idx)] = np.asarray(val).reshape((-1,) + (1,) * (out.ndim - 2))
+    return out
+
+
+def _prev_trace(mesh, A_right, m, eax, t, fn=None):
+    """Trace of the -x_m neighbour at each element's -x_m face (left boundary state
+    on the first element)."""
+    out = np.roll(A_right, 1, axis=eax)
+    if m in mesh.bc:
+        qb = np.asarray(mesh.bc[m][0](t), dtype=np.float64)
+        val = qb if fn is None else fn(qb)
+        idx = [slice(None)] * out.ndim
+        idx[eax] = 0
+        out[tuple(idx)] = np.asarray(val).reshape((-1,) + (1,) * (out.ndim - 2))
+    return out
+
+
 def _apply_D(D, A, axis):
     """(D A) along one node axis."""
     A = np.moveaxis(A, axis, -1)
@@ -121,73 +156,100 @@ def volume_term(mesh, U, phys):
     return out
 
 
-def inviscid_surface_term(mesh, U, phys):
+def _boundary_fluxes(mesh, U, phys, m, t):
+    """Interface fluxes on the +x_m and -x_m faces of every element (Dirichlet-penalty
+    exterior states on boundary faces)."""
+    g = phys.gamma
+    eax, nax = _AXES[m]
+    q_right = _face(U, mesh.p, nax)                   # this element, face +x_m
+    q_left = _face(U, 0, nax)                         # this element, face -x_m
+    q_next = _next_trace(mesh, q_left, m, eax, t)     # +x_m neighbour's -x_m face
+    f_right = gas.interface_flux(q_right, q_next, g, m, phys.diss)
+    f_left = np.roll(f_right, 1, axis=eax)            # flux on this element's -x_m face
+    if m in mesh.bc:
+        q_prev = _prev_trace(mesh, q_right, m, eax, t)
+        fb = gas.interface_flux(q_prev, q_left, g, m, phys.diss)
+        idx = [slice(None)] * f_left.ndim
+        idx[eax] = 0
+        f_left[tuple(idx)] = fb[tuple(idx)]
+    return q_right, q_left, f_right, f_left
+
+
+def inviscid_surface_term(mesh, U, phys, t=0.0):
     """SAT^I + diss^I on all six faces of every element."""
     g = phys.gamma
     p = mesh.p
     out = np.zeros_like(U)
     for m in range(3):
         eax, nax = _AXES[m]
-        q_right = _face(U, p, nax)                    # this element, face +x_m
-        q_left = _face(U, 0, nax)                     # this element, face -x_m
-        q_next = np.roll(q_left, -1, axis=eax)        # +x_m neighbour's -x_m face
-        f_right = gas.interface_flux(q_right, q_next, g, m, phys.diss)
-        f_left = np.roll(f_right, 1, axis=eax)        # flux on this element's -x_m face
+        q_right, q_left, f_right, f_left = _boundary_fluxes(mesh, U, phys, m, t)
         s = 2.0 / mesh.h[m]
         _add_face(out, p, nax, -s / mesh.omega[p] * (f_right - gas.euler_flux(q_right, g, m)))
         _add_face(out, 0, nax, s / mesh.omega[0] * (f_left - gas.euler_flux(q_left, g, m)))
     return out
 
 
-def entropy_gradients(mesh, U, phys):
+def entropy_gradients(mesh, U, phys, t=0.0):
     """BR1 theta_m = dw/dx_m, m = 0, 1, 2 (shape (3, 5, ...))."""
     W = gas.entropy_variables(U, phys.gamma)
     p = mesh.p
     theta = np.zeros((3,) + U.shape)
+
+    def wfun(q):
+        return gas.entropy_variables(q, phys.gamma)
     for m in range(3):
         eax, nax = _AXES[m]
-        t = _apply_D(mesh.D, W, nax)
+        dw = _apply_D(mesh.D, W, nax)
         w_right = _face(W, p, nax)
         w_left = _face(W, 0, nax)
-        w_next = np.roll(w_left, -1, axis=eax)
-        w_prev = np.roll(w_right, 1, axis=eax)
-        _add_face(t, p, nax, (0.5 * (w_right + w_next) - w_right) / mesh.omega[p])
-        _add_face(t, 0, nax, -(0.5 * (w_prev + w_left) - w_left) / mesh.omega[0])
-        theta[m] = (2.0 / mesh.h[m]) * t
+        w_next = _next_trace(mesh, w_left, m, eax, t, wfun)
+        w_prev = _prev_trace(mesh, w_right, m, eax, t, wfun)
+        _add_face(dw, p, nax, (0.5 * (w_right + w_next) - w_right) / mesh.omega[p])
+        _add_face(dw, 0, nax, -(0.5 * (w_prev + w_left) - w_left) / mesh.omega[0])
+        theta[m] = (2.0 / mesh.h[m]) * dw
     return theta
 
 
-def viscous_term(mesh, U, phys, return_parts=False):
-    """BR1 divergence of the viscous fluxes, with central interface SAT^V."""
+def viscous_term(mesh, U, phys, return_parts=False, t=0.0):
+    """BR1 divergence of the viscous fluxes, with central interface SAT^V (the interior
+    flux on boundary faces)."""
     p = mesh.p
-    theta = entropy_gradients(mesh, U, phys)
+    theta = entropy_gradients(mesh, U, phys, t)
     fv = gas.viscous_flux(U, theta, phys.gamma, phys.mu, phys.Pr, phys.R)
     out = np.zeros_like(U)
     for m in range(3):
         eax, nax = _AXES[m]
         F = fv[m]
-        t = _apply_D(mesh.D, F, nax)
+        dF = _apply_D(mesh.D, F, nax)
         f_right = _face(F, p, nax)
         f_left = _face(F, 0, nax)
         f_next = np.roll(f_left, -1, axis=eax)
         f_prev = np.roll(f_right, 1, axis=eax)
-        _add_face(t, p, nax, (0.5 * (f_right + f_next) - f_right) / mesh.omega[p])
-        _add_face(t, 0, nax, -(0.5 * (f_prev + f_left) - f_left) / mesh.omega[0])
-        out += (2.0 / mesh.h[m]) * t
+        if m in mesh.bc:
+            last = [slice(None)] * f_next.ndim
+            last[eax] = -1
+            first = [slice(None)] * f_prev.ndim
+            first[eax] = 0
+            f_next[tuple(last)] = f_right[tuple(last)]
+            f_prev[tuple(first)] = f_left[tuple(first)]
+        _add_face(dF, p, nax, (0.5 * (f_right + f_next) - f_right) / mesh.omega[p])
+        _add_face(dF, 0, nax, -(0.5 * (f_prev + f_left) - f_left) / mesh.omega[0])
+        out += (2.0 / mesh.h[m]) * dF
     if return_parts:
         return out, theta, fv
     return out
 
 
-def rhs(mesh, U, phys):
-    """f(u) of Eq. (ode): the right-hand side dq/dt of Eq. (compressible_ns_diss)."""
-    out = volume_term(mesh, U, phys) + inviscid_surface_term(mesh, U, phys)
+def rhs(mesh, U, phys, t=0.0):
+    """f(u) of Eq. (ode): the right-hand side dq/dt of Eq. (compressible_ns_diss) at time
+    t (t only enters through prescribed boundary states)."""
+    out = volume_term(mesh, U, phys) + inviscid_surface_term(mesh, U, phys, t)
     if phys.mu != 0.0:
-        out = out + viscous_term(mesh, U, phys)
+        out = out + viscous_term(mesh, U, phys, t=t)
     return out
 
 
-def rhs_term_magnitude(mesh, U, phys):
+def rhs_term_magnitude(mesh, U, phys, t=0.0):
     """Sum of the absolute values of the terms that rhs() adds at every node.
 
     Test infrastructure: the rounding error of any FP64 evaluation of the
@@ -204,14 +266,11 @@ def rhs_term_magnitude(mesh, U, phys):
         A = np.moveaxis(U, nax, -1)
         F = gas.ec_flux(A[..., :, None], A[..., None, :], g, m)
         T += s * np.moveaxis(np.einsum("ij,...ij->...i", np.abs(2.0 * mesh.D), np.abs(F)), -1, nax)
-        q_right = _face(U, p, nax)
-        q_left = _face(U, 0, nax)
-        f_right = gas.interface_flux(q_right, np.roll(q_left, -1, axis=eax), g, m, phys.diss)
-        f_left = np.roll(f_right, 1, axis=eax)
+        q_right, q_left, f_right, f_left = _boundary_fluxes(mesh, U, phys, m, t)
         _add_face(T, p, nax, s / mesh.omega[p] * (np.abs(f_right) + np.abs(gas.euler_flux(q_right, g, m))))
         _add_face(T, 0, nax, s / mesh.omega[0] * (np.abs(f_left) + np.abs(gas.euler_flux(q_left, g, m))))
     if phys.mu != 0.0:
-        _, theta, fv = viscous_term(mesh, U, phys, return_parts=True)
+        _, theta, fv = viscous_term(mesh, U, phys, return_parts=True, t=t)
         for m in range(3):
             eax, nax = _AXES[m]
             T += (2.0 / mesh.h[m]) * _apply_D(np.abs(mesh.D), np.abs(fv[m]), nax)

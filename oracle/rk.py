@@ -57,11 +57,12 @@ class StepResult:
     pass
 
 
-def rk_step(mesh, U, dt, phys, tab, mode="local", delta_floor=relax.DELTA_FLOOR, rhs=None):
-    """One relaxed RK step from U (shape mesh.shape).  Returns a StepResult.
+def rk_step(mesh, U, dt, phys, tab, mode="local", delta_floor=relax.DELTA_FLOOR, rhs=None, t=0.0):
+    """One relaxed RK step from U (shape mesh.shape) at time t.  Returns a StepResult.
 
-    rhs(mesh, U, phys) defaults to dg.rhs; tests pass a perturbed one to measure
-    how the relaxation parameters respond to last-bit changes of f."""
+    rhs(mesh, U, phys, t=...) defaults to dg.rhs; tests pass a perturbed one to
+    measure how the relaxation parameters respond to last-bit changes of f.  Stage i
+    is evaluated at t + c_i dt (prescribed boundary states depend on it)."""
     rhs = dg.rhs if rhs is None else rhs
     g = phys.gamma
     A_tab, b = tab["A"], tab["b"]
@@ -75,7 +76,7 @@ def rk_step(mesh, U, dt, phys, tab, mode="local", delta_floor=relax.DELTA_FLOOR,
         for j in range(i):
             if A_tab[i, j] != 0.0:
                 Y = Y + dt * A_tab[i, j] * ks[j]
-        k = rhs(mesh, Y, phys)
+        k = rhs(mesh, Y, phys, t=t + tab["c"][i] * dt)
         ks.append(k)
         E.append(dg.entropy_rate(mesh, Y, k, phys))
         if i > 0 and b[i] != 0.0:
@@ -122,7 +123,7 @@ def advance(mesh, U, dt, nsteps, phys, tab, mode="local", t0=0.0, delta_floor=re
     t = t0
     hist = []
     for _ in range(nsteps):
-        r = rk_step(mesh, U, dt, phys, tab, mode=mode, delta_floor=delta_floor, rhs=rhs)
+        r = rk_step(mesh, U, dt, phys, tab, mode=mode, delta_floor=delta_floor, rhs=rhs, t=t)
         U = r.U
         t = t + r.gamma * dt
         hist.append(r)

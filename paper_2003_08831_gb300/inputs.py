@@ -14,6 +14,15 @@ CUDA path and the CPU oracle receive states built here.
   benchmark): V_0 = L = rho_0 = 1, u = sin x cos y cos z, v = -cos x sin y cos z,
   w = 0, p = p_0 + (cos 2x + cos 2y)(cos 2z + 2)/16, p_0 = 1/(gamma M^2),
   rho = p/p_0 (isothermal start).
+* Viscous shock, Section 4.1.2 (Pr = 3/4, where the total enthalpy is constant
+  across the shock and the momentum and energy equations reduce to one ODE for
+  V = u/u_L).  Readings: the shock-frame upstream state (x -> -inf) is rho = u = 1,
+  p = 1/(gamma M^2); mu = 1/Re (unit length); V_f = u_R/u_L from the
+  Rankine--Hugoniot relations, (2 + (gamma-1) M^2)/((gamma+1) M^2); the implicit
+  solution is x = (alpha/2) [log|(V-1)(V-V_f)| + (1+V_f)/(1-V_f) log|(V-1)/(V-V_f)|]
+  (the printed form lacks the bracket; differentiating this one gives the ODE
+  alpha V V' = (V-1)(V-V_f)); the "uniform translation" moves the frame with the
+  upstream gas at rest: lab velocity u - 1, shock at x = -t.
 * Noise: SplitMix64 (Steele, Lea & Flood 2014) keyed by (seed, counter).
 """
 import numpy as np
@@ -121,3 +130,49 @@ def batch_instances(count=256, seed=SEED, nmin=4, nmax=12, pmin=2, pmax=5, box=1
             "box": box,
         })
     return out
+
+
+def viscous_shock_parameters(mach=2.5, reynolds=10.0, prandtl=0.75, gamma=1.4):
+    """Constants of the viscous-shock solution: upstream p, mu, V_f, alpha, total enthalpy."""
+    p_up = 1.0 / (gamma * mach * mach)
+    mu = 1.0 / reynolds
+    v_f = (2.0 + (gamma - 1.0) * mach * mach) / ((gamma + 1.0) * mach * mach)
+    alpha = 2.0 * gamma / (gamma + 1.0) * mu / prandtl          # mass flux rho u = 1
+    enthalpy = gamma / (gamma - 1.0) * p_up + 0.5
+    return {"p_up": p_up, "mu": mu, "v_f": v_f, "alpha": alpha, "H": enthalpy, "gamma": gamma,
+            "mach": mach, "reynolds": reynolds, "prandtl": prandtl}
+
+
+def viscous_shock_velocity(xi, prm):
+    """V(xi) in (V_f, 1) from the implicit solution by bisection to the last bit."""
+    xi = np.asarray(xi, dtype=np.float64)
+    vf, alpha = prm["v_f"], prm["alpha"]
+    c = (1.0 + vf) / (1.0 - vf)
+    lo = np.full(xi.shape, vf)
+    hi = np.ones(xi.shape)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        with np.errstate(divide="ignore"):
+            x_mid = 0.5 * alpha * (np.log((1.0 - mid) * (mid - vf)) + c * np.log((1.0 - mid) / (mid - vf)))
+        # x(V) decreases with V: x(mid) > xi means the root lies above mid
+        above = x_mid > xi
+        lo = np.where(above, mid, lo)
+        hi = np.where(above, hi, mid)
+    return 0.5 * (lo + hi)
+
+
+def viscous_shock_primitives(x, t, prm, speed=-1.0):
+    """(rho, u, v, w, p) of the viscous shock at lab position x and time t: the shock-frame
+    profile at xi = x - speed t, lab velocity u_shock + speed."""
+    v = viscous_shock_velocity(np.asarray(x, dtype=np.float64) - speed * t, prm)
+    g = prm["gamma"]
+    u = v                     # u_L = 1
+    rho = 1.0 / u             # mass flux 1
+    p = (g - 1.0) / g * rho * (prm["H"] - 0.5 * u * u)
+    z = np.zeros_like(rho)
+    return rho, u + speed, z, z.copy(), p
+
+
+def viscous_shock_state(x, t, prm, speed=-1.0):
+    rho, u, v, w, p = viscous_shock_primitives(x, t, prm, speed)
+    return conserved(rho, u, v, w, p, prm["gamma"])

@@ -133,9 +133,9 @@ def gamma_sensitivity(mesh, U, dt, nsteps, phys, tab, mode, hist, seeds=4, eps=E
     for seed in range(seeds):
         rng = np.random.default_rng(1000 + seed)
 
-        def noisy(m_, U_, p_):
-            R = dg.rhs(m_, U_, p_)
-            T = dg.rhs_term_magnitude(m_, U_, p_)
+        def noisy(m_, U_, p_, t=0.0):
+            R = dg.rhs(m_, U_, p_, t)
+            T = dg.rhs_term_magnitude(m_, U_, p_, t)
             return R + 2 * eps * T * rng.standard_normal(R.shape)
         _, _, h2 = rk.advance(mesh, U, dt, nsteps, phys, tab, mode=mode, rhs=noisy)
         dg_ = np.maximum(dg_, np.abs(np.array([h.gamma for h in h2]) - g0) / g0)
