@@ -94,6 +94,38 @@ int es_rhs(es_ctx* ctx, const double* q, double* dqdt, double* E_elem, void* str
 /* eta_elem[K] = eta_kappa(q) = 1^T P S_kappa (Section 3.2), S = -rho s/(gamma-1). */
 int es_entropy(es_ctx* ctx, const double* q, double* eta_elem, void* stream);
 
+/* Boundary treatment of direction dir (0, 1, 2 = x1, x2, x3) of a context
+ * (Section 4.1.2 prescribes boundary data by penalising the numerical solution
+ * against a given state; the penalty form is not printed).  Every direction is
+ * periodic after es_create.  For kind != ES_BC_PERIODIC the faces x_dir = lo and
+ * x_dir = hi are Dirichlet-penalty boundaries: the inviscid SAT uses the
+ * interface flux between the element's trace and the prescribed exterior state
+ * q_b (f_num(q_b, q) on the lo side, f_num(q, q_b) on the hi side), the BR1
+ * gradient lifts toward (w + w(q_b))/2, and the viscous boundary flux is the
+ * interior one.  q_b is evaluated on the device at each stage's time
+ * t + c_i dt (es_advance: t is its time argument; es_rhs: the time set by
+ * es_set_time, initially 0).
+ *   ES_BC_STATE          params[10] = q_b on the lo side, then on the hi side
+ *                        (conserved variables, physical).
+ *   ES_BC_VISCOUS_SHOCK  params[4] = {Mach > 1, Reynolds > 0, Prandtl > 0,
+ *                        speed}: the viscous-shock solution of Section 4.1.2
+ *                        along dir (shock-frame upstream rho = u = 1,
+ *                        p = 1/(gamma M^2), mu = 1/Re, V(x) from its implicit
+ *                        solution, total enthalpy constant; exact for Pr = 3/4
+ *                        and mu, Pr of the context equal to these), seen from a
+ *                        frame moving with velocity speed: the shock is at
+ *                        x_dir = speed t (speed = -1: upstream gas at rest).
+ * Batches are periodic.  Errors: ES_ERR_INVALID for a bad direction, kind or
+ * parameter list; ES_ERR_NOMEM if the boundary workspace cannot be allocated. */
+#define ES_BC_PERIODIC 0
+#define ES_BC_STATE 1
+#define ES_BC_VISCOUS_SHOCK 2
+int es_set_boundary(es_ctx* ctx, int dir, int kind, const double* params, int nparams);
+
+/* Sets the time at which es_rhs evaluates prescribed boundary states (host value;
+ * synchronous).  ES_ERR_INVALID for a non-finite t. */
+int es_set_time(es_ctx* ctx, double t);
+
 /* One relaxation (last row of Eq. (relaxation-local-gamma), Theorem 2.3):
  * for every element the root gamma_elem[e] > 0 of
  *   eta_e(u_old + g (u_new - u_old)) - eta_e(u_old) - g d_eta[e] = 0,

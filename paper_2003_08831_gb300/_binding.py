@@ -21,6 +21,7 @@ ES_ERR_TOO_LARGE = -7
 ES_RK_BS3, ES_RK_RK4 = 0, 1
 ES_FP64, ES_MIXED, ES_FP64X = 0, 1, 2
 ES_RELAX_NONE, ES_RELAX_LOCAL, ES_RELAX_GLOBAL = 0, 1, 2
+ES_BC_PERIODIC, ES_BC_STATE, ES_BC_VISCOUS_SHOCK = 0, 1, 2
 
 EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "es_advance",
            "es_advance_host", "es_node_coords", "es_status", "es_launch_count", "es_strerror",
@@ -28,7 +29,7 @@ EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "
            "es_autotune", "es_batch_create", "es_batch_destroy", "es_batch_nodes", "es_batch_node_coords",
            "es_batch_set_state", "es_batch_get_state", "es_batch_set_dt", "es_batch_autotune",
            "es_batch_volume_variant", "es_batch_advance", "es_batch_times", "es_batch_status",
-           "es_batch_launch_count", "es_reciprocal"]
+           "es_batch_launch_count", "es_reciprocal", "es_set_boundary", "es_set_time"]
 KERNEL_KINDS = ["prep", "face", "grad", "volume", "relax", "other"]
 
 
@@ -117,6 +118,10 @@ def load(path=None):
     lib.es_batch_launch_count.restype = ctypes.c_longlong
     lib.es_reciprocal.argtypes = [vp, vp, ctypes.c_longlong, vp]
     lib.es_reciprocal.restype = i
+    lib.es_set_boundary.argtypes = [vp, i, i, vp, i]
+    lib.es_set_boundary.restype = i
+    lib.es_set_time.argtypes = [vp, d]
+    lib.es_set_time.restype = i
     lib.es_strerror.argtypes = [i]
     lib.es_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -190,6 +195,18 @@ def es_rhs(ctx, q, dqdt, E_elem=None, stream=None):
 
 def es_entropy(ctx, q, eta_elem, stream=None):
     _check(load().es_entropy(ctx, _ptr(q), _ptr(eta_elem), _stream(stream)), "es_entropy")
+
+
+def es_set_boundary(ctx, direction, kind, params=None):
+    """params: host sequence of doubles (10 for ES_BC_STATE, 4 for ES_BC_VISCOUS_SHOCK)."""
+    n = 0 if params is None else len(params)
+    buf = (ctypes.c_double * max(n, 1))(*([] if params is None else [float(v) for v in params]))
+    _check(load().es_set_boundary(ctx, int(direction), int(kind), ctypes.cast(buf, ctypes.c_void_p) if n else None, n),
+           "es_set_boundary")
+
+
+def es_set_time(ctx, t):
+    _check(load().es_set_time(ctx, float(t)), "es_set_time")
 
 
 def es_relax_step(ctx, u_old, u_new, d_eta, gamma_elem, gamma, u_out, stream=None):

@@ -81,6 +81,7 @@ struct Tableau {
   int s;          // stages entering u_new
   double a[4][4];
   double b[4];
+  double c[4];    // stage times (boundary states are evaluated at t + c_i dt)
 };
 
 Tableau tableau(int rk) {
@@ -90,6 +91,8 @@ Tableau tableau(int rk) {
     t.s = 3;
     t.a[1][0] = 0.5;
     t.a[2][1] = 0.75;
+    t.c[1] = 0.5;
+    t.c[2] = 0.75;
     t.b[0] = 2.0 / 9.0;
     t.b[1] = 1.0 / 3.0;
     t.b[2] = 4.0 / 9.0;
@@ -98,6 +101,9 @@ Tableau tableau(int rk) {
     t.a[1][0] = 0.5;
     t.a[2][1] = 0.5;
     t.a[3][2] = 1.0;
+    t.c[1] = 0.5;
+    t.c[2] = 0.5;
+    t.c[3] = 1.0;
     t.b[0] = 1.0 / 6.0;
     t.b[1] = 1.0 / 3.0;
     t.b[2] = 1.0 / 3.0;
@@ -199,6 +205,14 @@ int grid_for_sms(int sm_count, long long n, int block) {
 // A group: instances sharing the LGL degree and the physics, stored as one SoA
 // over the group's elements.  The single-instance context is a group of one;
 // a batch is one group per degree.
+// Dirichlet-penalty boundary data of a context (host copy; passed to k_bc_eval by value)
+struct BcSpec {
+  int kind[3];           // ES_BC_* per direction
+  double q[3][2][5];     // ES_BC_STATE: exterior states (left, right)
+  double vs[3][6];       // ES_BC_VISCOUS_SHOCK: V_f, alpha, H, speed, x_lo, x_hi
+  double gam;
+};
+
 struct Group {
   es_config cfg;  // physics (and, for a context, the mesh)
   int P1 = 0, Np = 0, K = 0, ninst = 0;
@@ -226,6 +240,10 @@ struct Group {
   GlobalRelaxState* gstate = nullptr;    // global relaxation: [ninst]
   InstGeom* geom_dev = nullptr;
   int* elem_inst_dev = nullptr;
+  BcSpec bc;                             // boundary kinds and data (contexts only)
+  bool any_bc = false;
+  void* FL = nullptr;                    // -x_m boundary-face fluxes (tf bytes each)
+  double* bcz = nullptr;                 // [3][2][kBcVals] exterior values at the stage time
 };
 
 // Launch bookkeeping shared by a context or a batch.
@@ -390,6 +408,8 @@ void group_free(Group& g) {
   cudaFree(g.gstate);
   cudaFree(g.geom_dev);
   cudaFree(g.elem_inst_dev);
+  cudaFree(g.FL);
+  cudaFree(g.bcz);
   g = Group();
 }
 
@@ -459,19 +479,79 @@ int group_init(Group& g, const es_config* insts, int n, int stages, bool own_sta
   return rc;
 }
 
+// Exterior values of the Dirichlet-penalty boundaries at time *t + t_off: one thread per
+// (direction, side).  ES_BC_VISCOUS_SHOCK evaluates the Section 4.1.2 profile: V in
+// (V_f, 1) solves x - speed t = (alpha/2) [log((1-V)(V-V_f)) + (1+V_f)/(1-V_f)
+// log((1-V)/(V-V_f))] (bisection to the last bit), u = V, rho = 1/V, p from the constant
+// total enthalpy H, lab velocity u + speed along the direction.
+__global__ void k_bc_eval(BcSpec spec, const double* t, double t_off, double* out) {
+  const int i = threadIdx.x;
+  if (i >= 6) return;
+  const int m = i / 2, side = i % 2;
+  if (spec.kind[m] == ES_BC_PERIODIC) return;
+  const double g = spec.gam;
+  double q[5];
+  if (spec.kind[m] == ES_BC_STATE) {
+    for (int v = 0; v < 5; ++v) q[v] = spec.q[m][side][v];
+  } else {
+    const double vf = spec.vs[m][0], alpha = spec.vs[m][1], H = spec.vs[m][2], speed = spec.vs[m][3];
+    const double time = (t ? t[0] : 0.0) + t_off;
+    const double xi = spec.vs[m][4 + side] - speed * time;
+    const double c = (1.0 + vf) / (1.0 - vf);
+    double lo = vf, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      const double x = 0.5 * alpha * (log((1.0 - mid) * (mid - vf)) + c * log((1.0 - mid) / (mid - vf)));
+      if (x > xi) lo = mid;
+      else hi = mid;
+    }
+    const double u = 0.5 * (lo + hi);
+    const double rho = 1.0 / u;
+    const double p = (g - 1.0) / g * rho * (H - 0.5 * u * u);
+    const double ul = u + speed;
+    for (int v = 0; v < 5; ++v) q[v] = 0.0;
+    q[0] = rho;
+    q[1 + m] = rho * ul;
+    q[4] = p / (g - 1.0) + 0.5 * rho * ul * ul;
+  }
+  const double rho = q[0];
+  const double v0 = q[1] / rho, v1 = q[2] / rho, v2 = q[3] / rho;
+  const double p = (g - 1.0) * (q[4] - 0.5 * rho * (v0 * v0 + v1 * v1 + v2 * v2));
+  const double z1 = sqrt(rho / p);
+  double* o = out + i * kBcVals;
+  o[0] = z1;
+  o[1] = z1 * v0;
+  o[2] = z1 * v1;
+  o[3] = z1 * v2;
+  o[4] = sqrt(rho * p);
+  o[5] = sqrt(p / rho);
+  o[6] = rho * v0 / p;
+  o[7] = rho * v1 / p;
+  o[8] = rho * v2 / p;
+  o[9] = -rho / p;
+}
+
+void launch_bc_eval(const BcSpec& spec, const double* t, double t_off, double* out, cudaStream_t st) {
+  k_bc_eval<<<1, 32, 0, st>>>(spec, t, t_off, out);
+}
+
 int grid_for(const Engine& e, long long n, int block) { return grid_for_sms(e.sm_count, n, block); }
 
 // One stage's right-hand side into kout or d (+ element sums), on state u (+ pending
 // update) + dt sum_j coef[j] k[j].
-int run_stage(Engine& E, Group& g, const StagePrep& sp, const StageVol& sv, cudaStream_t st) {
+int run_stage(Engine& E, Group& g, const StagePrep& sp, const StageVol& sv, cudaStream_t st,
+              const double* t_dev = nullptr, double t_off = 0.0) {
   const bool ns = g.cfg.mu != 0.0;
+  if (g.any_bc) {  // exterior states at this stage's time t + c_i dt
+    timed(E, ES_KERNEL_OTHER, st, [&] { launch_bc_eval(g.bc, t_dev ? t_dev : g.t, t_off, g.bcz, st); });
+  }
   return dispatch(g, [&](auto L) {
     using Lc = decltype(L);
     timed(E, ES_KERNEL_PREP, st, [&] { Lc::prep(g.P, sp, g.aux, E.status, st, grid_for(E, g.N, 256)); });
     timed(E, ES_KERNEL_FACE, st,
-          [&] { Lc::face(g.P, g.aux, g.F, st, grid_for(E, 3LL * g.K * g.P1 * g.P1, 256)); });
+          [&] { Lc::face(g.P, g.aux, g.F, g.FL, st, grid_for(E, 3LL * g.K * g.P1 * g.P1, 256)); });
     if (ns) timed(E, ES_KERNEL_GRAD, st, [&] { Lc::grad(g.P, g.aux, g.fV, st, grid_for(E, g.N, 256)); });
-    timed(E, ES_KERNEL_VOLUME, st, [&] { Lc::volume(g.P, sv, g.aux, g.F, g.fV, ns, st, g.vol_variant); });
+    timed(E, ES_KERNEL_VOLUME, st, [&] { Lc::volume(g.P, sv, g.aux, g.F, g.FL, g.fV, ns, st, g.vol_variant); });
     return last_launch_error();
   });
 }
@@ -543,7 +623,7 @@ int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStre
     sv.A = relax ? g.A : nullptr;
     sv.A_scale = -T.b[i];
     sv.A_init = (i == 0);
-    rc = run_stage(E, g, sp, sv, st);
+    rc = run_stage(E, g, sp, sv, st, t, T.c[i] * g.P.g0.dt);
   }
   if (rc != ES_OK) return rc;
   StageRelax sr = relax_base(E, g);
@@ -732,6 +812,56 @@ int es_rhs(es_ctx* c, const double* q, double* dqdt, double* E_elem, void* strea
   sv.kout64 = dqdt;
   sv.E = E_elem;
   return run_stage(c->eng, c->g, sp, sv, st);
+}
+
+int es_set_boundary(es_ctx* c, int dir, int kind, const double* params, int nparams) {
+  if (!c || dir < 0 || dir > 2) return ES_ERR_INVALID;
+  Group& g = c->g;
+  BcSpec& b = g.bc;
+  if (kind == ES_BC_PERIODIC) {
+    b.kind[dir] = ES_BC_PERIODIC;
+  } else if (kind == ES_BC_STATE) {
+    if (!params || nparams != 10) return ES_ERR_INVALID;
+    for (int s = 0; s < 2; ++s) {
+      const double* q = params + 5 * s;
+      const double p = (g.cfg.gamma_gas - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+      if (!(q[0] > 0.0) || !(p > 0.0)) return ES_ERR_INVALID;
+      for (int v = 0; v < 5; ++v) b.q[dir][s][v] = q[v];
+    }
+    b.kind[dir] = ES_BC_STATE;
+  } else if (kind == ES_BC_VISCOUS_SHOCK) {
+    // params: Mach number, Reynolds number, Prandtl number, translation speed
+    if (!params || nparams != 4) return ES_ERR_INVALID;
+    const double M = params[0], Re = params[1], Pr = params[2], speed = params[3];
+    const double gm = g.cfg.gamma_gas;
+    if (!(M > 1.0) || !(Re > 0.0) || !(Pr > 0.0) || !std::isfinite(speed)) return ES_ERR_INVALID;
+    b.vs[dir][0] = (2.0 + (gm - 1.0) * M * M) / ((gm + 1.0) * M * M);  // V_f
+    b.vs[dir][1] = 2.0 * gm / (gm + 1.0) * (1.0 / Re) / Pr;          // alpha (mass flux 1)
+    b.vs[dir][2] = gm / (gm - 1.0) / (gm * M * M) + 0.5;              // total enthalpy
+    b.vs[dir][3] = speed;
+    b.vs[dir][4] = g.cfg.lo[dir];
+    b.vs[dir][5] = g.cfg.hi[dir];
+    b.kind[dir] = ES_BC_VISCOUS_SHOCK;
+  } else {
+    return ES_ERR_INVALID;
+  }
+  b.gam = g.cfg.gamma_gas;
+  g.any_bc = b.kind[0] != ES_BC_PERIODIC || b.kind[1] != ES_BC_PERIODIC || b.kind[2] != ES_BC_PERIODIC;
+  int rc = ES_OK;
+  if (g.any_bc && !g.FL) rc = dev_alloc_bytes(&g.FL, 15 * size_t(g.K) * g.P1 * g.P1 * g.tf);
+  if (rc == ES_OK && g.any_bc && !g.bcz) {
+    rc = dev_alloc(&g.bcz, 6 * kBcVals);
+    if (rc == ES_OK) rc = cuda_check(cudaMemset(g.bcz, 0, sizeof(double) * 6 * kBcVals));
+  }
+  if (rc != ES_OK) return rc;
+  for (int m = 0; m < 3; ++m) g.P.bc[m] = b.kind[m] != ES_BC_PERIODIC ? 1 : 0;
+  g.P.bcz = g.bcz;
+  return ES_OK;
+}
+
+int es_set_time(es_ctx* c, double t) {
+  if (!c || !std::isfinite(t)) return ES_ERR_INVALID;
+  return cuda_check(cudaMemcpy(c->g.t, &t, sizeof(double), cudaMemcpyHostToDevice));
 }
 
 int es_entropy(es_ctx* c, const double* q, double* eta, void* stream) {

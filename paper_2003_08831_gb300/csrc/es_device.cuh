@@ -18,6 +18,11 @@ constexpr int kMaxP1 = 6;
 constexpr int kStatusNonphysical = 1;
 constexpr int kStatusNoRoot = 2;
 
+// Exterior values of a Dirichlet-penalty boundary, per direction and side, at the
+// current stage time: the parameter vector z1..z5, 1/z1 and the entropy variables
+// w2..w5 of the prescribed state (layout [3 directions][2 sides][kBcVals]).
+constexpr int kBcVals = 10;
+
 // Geometry of one periodic Cartesian instance (mesh) inside a group of
 // instances sharing the LGL degree; a single-instance context is a group of one.
 struct InstGeom {
@@ -66,6 +71,8 @@ struct Params {
   InstGeom g0;                 // the instance when geom is null (single-instance context)
   const InstGeom* geom;        // device table [ninst] (batches), or null
   const int* elem_inst;        // device [K]: instance of each element (batches), or null
+  int bc[3];                   // per direction: 0 periodic, 1 Dirichlet penalty (single instance)
+  const double* bcz;           // device [3][2][kBcVals] exterior values (see kBcVals), or null
 };
 
 template <typename T> __device__ __forceinline__ const FluxConst<T>& flux_const(const Params& P);
@@ -89,6 +96,20 @@ __device__ __forceinline__ int neighbour(const Params& P, int e, int m, int dir)
   else if (m == 1) ey = (ey + dir + G.ny) % G.ny;
   else ez = (ez + dir + G.nz) % G.nz;
   return G.off + ex + G.nx * (ey + G.ny * ez);
+}
+
+// Dirichlet-penalty boundary faces: element e is first (side 0) or last (side 1)
+// along a non-periodic direction m
+__device__ __forceinline__ bool at_boundary(const Params& P, int e, int m, int side) {
+  if (!P.bc[m]) return false;
+  const InstGeom& G = geom_of(P, inst_of(P, e));
+  const int le = e - G.off;
+  const int idx = m == 0 ? le % G.nx : (m == 1 ? (le / G.nx) % G.ny : le / (G.nx * G.ny));
+  const int n = m == 0 ? G.nx : (m == 1 ? G.ny : G.nz);
+  return side == 0 ? idx == 0 : idx == n - 1;
+}
+__device__ __forceinline__ const double* bc_values(const Params& P, int m, int side) {
+  return P.bcz + (m * 2 + side) * kBcVals;
 }
 
 // node index of position i on the line (a, b) in direction m

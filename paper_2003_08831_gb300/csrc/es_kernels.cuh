@@ -360,8 +360,33 @@ __device__ __forceinline__ Zstate<TF> load_z(const TF* __restrict__ aux, long lo
   return s;
 }
 
+// interface flux f_num(L, R) of the EC flux with optional Rusanov dissipation
+template <typename TF>
+__device__ __forceinline__ void face_flux(const Zstate<TF>& L, TF izL, const Zstate<TF>& R, TF izR, int m,
+                                          const FluxConst<TF>& C, int diss, TF f[5]) {
+  ec_flux(L, R, m, C, f);
+  if (diss) {
+    TF qL[5], qR[5], lL, lR;
+    z_to_q(L, izL, C, qL, lL, m);
+    z_to_q(R, izR, C, qR, lR, m);
+    const TF lam = TF(0.5) * fmax(lL, lR);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) f[v] -= lam * (qR[v] - qL[v]);
+  }
+}
+
+// a prescribed boundary state's parameter vector and 1/z1 in the flux precision
+template <typename TF>
+__device__ __forceinline__ Zstate<TF> bc_z(const double* v, TF& iz) {
+  Zstate<TF> z;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) z.z[c] = tf_from_double<TF>(v[c]);
+  iz = tf_from_double<TF>(v[5]);
+  return z;
+}
+
 template <int P1, typename TF>
-__global__ void k_face(Params P, const TF* __restrict__ aux, TF* __restrict__ F) {
+__global__ void k_face(Params P, const TF* __restrict__ aux, TF* __restrict__ F, TF* __restrict__ FL) {
   constexpr int P2 = P1 * P1, Np = P1 * P2;
   const long long N = (long long)P.K * Np;
   const long long total = 3LL * P.K * P2;
@@ -372,23 +397,30 @@ __global__ void k_face(Params P, const TF* __restrict__ aux, TF* __restrict__ F)
     const long long rem = idx - (long long)m * P.K * P2;
     const int e = int(rem / P2), ab = int(rem % P2);
     const int a = ab % P1, b = ab / P1;
-    const int en = neighbour(P, e, m, +1);
     const long long gL = (long long)e * Np + line_node<P1>(m, a, b, P1 - 1);
-    const long long gR = (long long)en * Np + line_node<P1>(m, a, b, 0);
     const Zstate<TF> L = load_z<P1, TF>(aux, N, gL);
-    const Zstate<TF> R = load_z<P1, TF>(aux, N, gR);
-    TF f[5];
-    ec_flux(L, R, m, C, f);
-    if (P.diss) {
-      TF qL[5], qR[5], lL, lR;
-      z_to_q(L, aux[5 * N + gL], C, qL, lL, m);
-      z_to_q(R, aux[5 * N + gR], C, qR, lR, m);
-      const TF lam = TF(0.5) * fmax(lL, lR);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) f[v] -= lam * (qR[v] - qL[v]);
+    const TF izL = aux[5 * N + gL];
+    Zstate<TF> R;
+    TF izR;
+    if (at_boundary(P, e, m, 1)) {  // +x_m boundary: prescribed exterior state
+      R = bc_z<TF>(bc_values(P, m, 1), izR);
+    } else {
+      const long long gR = (long long)neighbour(P, e, m, +1) * Np + line_node<P1>(m, a, b, 0);
+      R = load_z<P1, TF>(aux, N, gR);
+      izR = aux[5 * N + gR];
     }
+    TF f[5];
+    face_flux(L, izL, R, izR, m, C, P.diss, f);
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[((long long)(m * 5 + v) * P.K + e) * P2 + ab] = f[v];
+    if (at_boundary(P, e, m, 0)) {  // -x_m boundary face of this element, into FL
+      TF izB;
+      const Zstate<TF> B = bc_z<TF>(bc_values(P, m, 0), izB);
+      const long long g0 = (long long)e * Np + line_node<P1>(m, a, b, 0);
+      face_flux(B, izB, load_z<P1, TF>(aux, N, g0), aux[5 * N + g0], m, C, P.diss, f);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) FL[((long long)(m * 5 + v) * P.K + e) * P2 + ab] = f[v];
+    }
   }
 }
 
@@ -440,10 +472,20 @@ __global__ void __launch_bounds__(THREADS) k_grad(Params P, const TF* __restrict
       }
       if (im == P1 - 1 || im == 0) {
         const bool right = (im == P1 - 1);
-        const int en = neighbour(P, e, m, right ? +1 : -1);
-        const long long gn = (long long)en * Np + line_node<P1>(m, a, b, right ? 0 : P1 - 1);
-        const TF zn1 = aux[gn];
-        const TF wn[4] = {zn1 * aux[N + gn], zn1 * aux[2 * N + gn], zn1 * aux[3 * N + gn], -zn1 * zn1};
+        TF wn[4];
+        if (at_boundary(P, e, m, right ? 1 : 0)) {  // prescribed exterior w2..w5
+          const double* bv = bc_values(P, m, right ? 1 : 0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) wn[c] = tf_from_double<TF>(bv[6 + c]);
+        } else {
+          const int en = neighbour(P, e, m, right ? +1 : -1);
+          const long long gn = (long long)en * Np + line_node<P1>(m, a, b, right ? 0 : P1 - 1);
+          const TF zn1 = aux[gn];
+          wn[0] = zn1 * aux[N + gn];
+          wn[1] = zn1 * aux[2 * N + gn];
+          wn[2] = zn1 * aux[3 * N + gn];
+          wn[3] = -zn1 * zn1;
+        }
         const TF sg = right ? TF(0.5) * iw : TF(-0.5) * iw;
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[c] += sg * (wn[c] - ws[c * EPB * Np + t]);
@@ -482,7 +524,8 @@ __global__ void __launch_bounds__(THREADS) k_grad(Params P, const TF* __restrict
 // ---------------------------------------------------------------------------
 template <int P1, typename TF, bool NS, int EPB, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const TF* __restrict__ aux,
-                                                   const TF* __restrict__ F, const TF* __restrict__ fV) {
+                                                   const TF* __restrict__ F, const TF* __restrict__ FL,
+                                                   const TF* __restrict__ fV) {
   constexpr int P2 = P1 * P1, Np = P1 * P2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TF* za = reinterpret_cast<TF*>(smem_raw);            // [kAux][EPB*Np]
@@ -535,11 +578,14 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
         }
       }
       // interface terms: + (1/omega_p) f_num(+face) at i = p, - (1/omega_0) f_num(-face) at i = 0
-      const int em = neighbour(P, e, m, -1);
+      // the -x_m face flux: the -x_m neighbour's +x_m flux, or the boundary flux in FL
+      const bool lo_b = at_boundary(P, e, m, 0);
+      const TF* Fm = lo_b ? FL : F;
+      const int em = lo_b ? e : neighbour(P, e, m, -1);
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         r[P1 - 1][v] += iw * F[((long long)(m * 5 + v) * P.K + e) * P2 + ab];
-        r[0][v] -= iw * F[((long long)(m * 5 + v) * P.K + em) * P2 + ab];
+        r[0][v] -= iw * Fm[((long long)(m * 5 + v) * P.K + em) * P2 + ab];
       }
       if constexpr (NS) {
         // viscous divergence (2/h_m)[D F^V_m + lifting]; enters with the opposite sign of r
@@ -550,8 +596,9 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
           TF fl[P1];
 #pragma unroll
           for (int j = 0; j < P1; ++j) fl[j] = fc[(long long)e * Np + line_node<P1>(m, a, b, j)];
-          const TF f_next = fc[(long long)ep * Np + line_node<P1>(m, a, b, 0)];
-          const TF f_prev = fc[(long long)em * Np + line_node<P1>(m, a, b, P1 - 1)];
+          // boundary faces take the interior viscous flux (no viscous penalty)
+          const TF f_next = at_boundary(P, e, m, 1) ? fl[P1 - 1] : fc[(long long)ep * Np + line_node<P1>(m, a, b, 0)];
+          const TF f_prev = lo_b ? fl[0] : fc[(long long)em * Np + line_node<P1>(m, a, b, P1 - 1)];
 #pragma unroll
           for (int i = 0; i < P1; ++i) {
             TF s = TF(0);
@@ -1203,8 +1250,8 @@ void Launcher<P1, TF>::prep(const Params& P, const StagePrep& sp, void* aux, int
 }
 
 template <int P1, typename TF>
-void Launcher<P1, TF>::face(const Params& P, const void* aux, void* F, cudaStream_t st, int grid) {
-  k_face<P1, TF><<<grid, 256, 0, st>>>(P, static_cast<const TF*>(aux), static_cast<TF*>(F));
+void Launcher<P1, TF>::face(const Params& P, const void* aux, void* F, void* FL, cudaStream_t st, int grid) {
+  k_face<P1, TF><<<grid, 256, 0, st>>>(P, static_cast<const TF*>(aux), static_cast<TF*>(F), static_cast<TF*>(FL));
 }
 
 template <int P1, typename TF>
@@ -1241,26 +1288,27 @@ cudaError_t Launcher<P1, TF>::volume_setup() {
 }
 
 template <int P1, typename TF, int V>
-void volume_v(const Params& P, const StageVol& sv, const TF* aux, const TF* F, const TF* fV, bool ns,
+void volume_v(const Params& P, const StageVol& sv, const TF* aux, const TF* F, const TF* FL, const TF* fV, bool ns,
               cudaStream_t st) {
   using C = VolCfg<P1, V>;
   const int grid = (P.K + C::EPB - 1) / C::EPB;
   const size_t smem = vol_smem_bytes<P1, C::EPB>(sizeof(TF));
   if (ns)
-    k_volume<P1, TF, true, C::EPB, C::THREADS><<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, fV);
+    k_volume<P1, TF, true, C::EPB, C::THREADS><<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, FL, fV);
   else
-    k_volume<P1, TF, false, C::EPB, C::THREADS><<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, fV);
+    k_volume<P1, TF, false, C::EPB, C::THREADS><<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, FL, fV);
 }
 
 template <int P1, typename TF>
-void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* aux, const void* F, const void* fV,
+void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* aux, const void* F, const void* FL, const void* fV,
                               bool ns, cudaStream_t st, int variant) {
   const TF* a = static_cast<const TF*>(aux);
   const TF* f = static_cast<const TF*>(F);
+  const TF* fl = static_cast<const TF*>(FL);
   const TF* v = static_cast<const TF*>(fV);
-  if (variant == 1) volume_v<P1, TF, 1>(P, sv, a, f, v, ns, st);
-  else if (variant == 2) volume_v<P1, TF, 2>(P, sv, a, f, v, ns, st);
-  else volume_v<P1, TF, 0>(P, sv, a, f, v, ns, st);
+  if (variant == 1) volume_v<P1, TF, 1>(P, sv, a, f, fl, v, ns, st);
+  else if (variant == 2) volume_v<P1, TF, 2>(P, sv, a, f, fl, v, ns, st);
+  else volume_v<P1, TF, 0>(P, sv, a, f, fl, v, ns, st);
 }
 
 template <int P1, typename TF>

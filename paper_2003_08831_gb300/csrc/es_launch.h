@@ -86,12 +86,13 @@ constexpr int kVolumeVariants = 3;
 template <int P1, typename TF>
 struct Launcher {
   static void prep(const Params& P, const StagePrep& sp, void* aux, int* status, cudaStream_t st, int grid);
-  static void face(const Params& P, const void* aux, void* F, cudaStream_t st, int grid);
+  // FL: -x_m boundary-face fluxes of the first elements along non-periodic directions (or null)
+  static void face(const Params& P, const void* aux, void* F, void* FL, cudaStream_t st, int grid);
   static void grad(const Params& P, const void* aux, void* fV, cudaStream_t st, int grid);
   static cudaError_t volume_setup();
   // variant: volume tile (elements per CTA, threads), 0..kVolumeVariants-1
-  static void volume(const Params& P, const StageVol& sv, const void* aux, const void* F, const void* fV, bool ns,
-                     cudaStream_t st, int variant);
+  static void volume(const Params& P, const StageVol& sv, const void* aux, const void* F, const void* FL,
+                     const void* fV, bool ns, cudaStream_t st, int variant);
   static void relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid);
   static void entropy(const Params& P, const double* q, double* eta, cudaStream_t st, int grid);
   static void global_relax(const Params& P, const GlobalRelaxArgs& ga, cudaStream_t st, int grid, int iterations);

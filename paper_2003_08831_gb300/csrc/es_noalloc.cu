@@ -124,9 +124,9 @@ extern "C" int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqd
   rc = dispatch_p1(P1, fp64, [&](auto L) {
     using Lc = decltype(L);
     Lc::prep(P, sp, aux, status, st, grid_for_sms(sms, N, 256));
-    Lc::face(P, aux, F, st, grid_for_sms(sms, 3LL * K * P1 * P1, 256));
+    Lc::face(P, aux, F, nullptr, st, grid_for_sms(sms, 3LL * K * P1 * P1, 256));
     if (ns) Lc::grad(P, aux, fV, st, grid_for_sms(sms, N, 256));
-    Lc::volume(P, sv, aux, F, fV, ns, st, 0);
+    Lc::volume(P, sv, aux, F, nullptr, fV, ns, st, 0);
     return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
   });
   return rc;

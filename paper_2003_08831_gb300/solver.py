@@ -140,6 +140,15 @@ class Solver:
                 c["interface_diss"], c["relax"], c["rk"], c["precision"], c["delta_floor"], device=device)
         return s, s.to_device(q), h["t"], h["step"], h["dt"]
 
+    def set_boundary(self, direction, kind, params=None):
+        """Dirichlet-penalty boundaries on the faces of `direction` (ES_BC_STATE with the two
+        exterior states, ES_BC_VISCOUS_SHOCK with (Mach, Re, Pr, speed)); ES_BC_PERIODIC resets."""
+        B.es_set_boundary(self.ctx, direction, kind, params)
+
+    def set_time(self, t):
+        """Time at which rhs() evaluates prescribed boundary states."""
+        B.es_set_time(self.ctx, t)
+
     def autotune(self, q, stream=None):
         B.es_autotune(self.ctx, q, stream)
 
