@@ -241,7 +241,8 @@ int es_batch_status(es_batch* b, void* stream);
 long long es_batch_launch_count(const es_batch* b);
 
 /* out[i] = 1/x[i] (device arrays) with the library's FP64 reciprocal: the
- * hardware approximation refined by two Newton--Raphson steps, used in the
+ * hardware approximation refined by one third-order step r (1 + e + e^2),
+ * e = 1 - x r (within one ulp, not correctly rounded), used in the
  * flux, thermodynamics and relaxation kernels in place of IEEE division.
  * Exposed so that it can be checked against IEEE division; x must be normal. */
 int es_reciprocal(const double* x, double* out, long long n, void* stream);

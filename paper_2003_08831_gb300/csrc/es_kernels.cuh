@@ -4,16 +4,18 @@
 //
 // Stage pipeline (Eq. (RK-step), Eq. (compressible_ns_diss)):
 //   k_prep    y^i = u + dt sum_j a_ij k_j (fused relaxed update of the previous
-//             step), parameter-vector state z, ln z1, ln z5 per node; for i > 1
-//             the increment w(y^i) - w(u) of the entropy variables.
-//   k_face    interface flux f*(q-, q+) - diss lambda/2 (q+ - q-) per face node.
+//             step), parameter-vector state z and 1/z1 per node; for i > 1 the
+//             increment w(y^i) - w(u) of the entropy variables.
+//   k_face    interface flux f*(q-, q+) - diss lambda/2 (q+ - q-) per face node
+//             (prescribed exterior states on Dirichlet-penalty boundary faces).
 //   k_grad    (Navier--Stokes) BR1 entropy-variable gradients and the viscous
 //             flux F^V_m = C_mj theta_j per node.
 //   k_volume  per element: flux-differencing sums along every LGL line,
 //             interface terms, viscous divergence; k_i, and the element sums
 //             (eta' f)(y^i) (Eq. (eta-est-1-RK)) and the relaxation term A.
-//   k_relax   per element (one warp): gamma_kappa of
-//             Eq. (relaxation-local-gamma); atomic min into gamma.
+//   k_relax   per element (a group of 8-32 lanes): gamma_kappa of
+//             Eq. (relaxation-local-gamma); atomic min into gamma (k_relax_ff:
+//             the same in float-float for the mixed and ES_FP64X modes).
 //   k_scalar  gamma = min gamma_kappa, t += gamma dt (Eq. (t-n-gamma)).
 #pragma once
 #include <cuda_runtime.h>
@@ -745,12 +747,13 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
 }
 
 // ---------------------------------------------------------------------------
-// Relaxation (one warp per element).  Per node: X0 = d_rho/rho,
+// Relaxation (one lane group per element, RelaxGroup).  Per node: X0 = d_rho/rho,
 // dv = (d_m - v d_rho)/rho, Y0 = (gam-1)(d_E - v.d_m + |v|^2 d_rho/2)/p,
 // V2 = rho |dv|^2/p, c = P_n rho.  r(g) = sum_n c D_n(g)/rho_n + g A,
 // r'(g) = sum_n c dD_n/dg + A; a = r''(0)/2 = sum c (X0^2 + (X0-Y0)^2/(gam-1) + V2)/2.
-// Newton from the root -A/a of the quadratic model, safeguarded by the bracket
-// [lo, hi] (r(lo) <= 0 < r(hi)); r is convex, so Newton converges from above.
+// Newton from the root of the cubic model a g^2 + b g^3 + A g (b from
+// relax_node_cubic), safeguarded by the bracket [lo, hi] (r(lo) <= 0 < r(hi)); r is
+// convex, so Newton converges from above.
 // Near the root the error after a step s is ~ s^2 r''/(2 r') ~ s^2/g, so a step
 // |s| <= 1e-8 g leaves an error ~1e-16 g: the updated iterate is returned
 // without another evaluation.
