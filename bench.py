@@ -228,6 +228,41 @@ def make_solver(wl):
     return Solver(wl["p"], (n, n, n), lo, hi, mu=wl["mu"], Pr=0.72, precision=wl["precision"])
 
 
+def state_error(q, ref):
+    """Relative L2 over all conserved variables and per-variable max error relative to the
+    variable's max |ref| (floored at 1e-3 of the largest), of a state against a reference."""
+    q = np.asarray(q, dtype=np.float64).reshape(5, -1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(5, -1)
+    d = q - ref
+    scale = np.maximum(np.max(np.abs(ref), axis=1), 1e-3 * np.max(np.abs(ref)))
+    return {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+            "max_rel_per_var": [float(v) for v in np.max(np.abs(d), axis=1) / scale]}
+
+
+def error_vs_fp64(wl, steps=20):
+    """The form's state after `steps` relaxed steps against the FP64 path (which matches
+    the oracle to 1e-12) from the same initial state and time step."""
+    from paper_2003_08831_gb300.solver import stable_dt
+    out = {}
+    for prec in (0, wl["precision"]):
+        w = dict(wl, precision=prec)
+        s = make_solver(w)
+        q0 = initial_state(s, w)
+        h = [(s.hi[m] - s.lo[m]) / s.n[m] for m in range(3)]
+        dt = stable_dt(q0, s.p, h, 0.5, mu=w["mu"])
+        q = s.to_device(q0)
+        s.advance(q, steps, dt)
+        if s.status() != 0:
+            raise RuntimeError("device status %d in the precision comparison" % s.status())
+        out[prec] = q.cpu().numpy()
+        s.close()
+        del q
+    r = state_error(out[wl["precision"]], out[0])
+    r["steps"] = steps
+    r["reference"] = "FP64 path, same initial state and dt"
+    return r
+
+
 def measure_device(wl, steps, warmup, dist=None, clocks_gpu=None):
     """Device-resident timing of `steps` relaxed steps (CUDA events on the launching stream)."""
     import torch
@@ -272,7 +307,7 @@ def measure_device(wl, steps, warmup, dist=None, clocks_gpu=None):
     return res
 
 
-def measure_batch(precision, steps, warmup, count=256):
+def measure_batch(precision, steps, warmup, count=256, ref_states=None, keep_states=False):
     """Config 5 form: `count` independent isentropic-vortex instances (seeded n in 4..12,
     p in 2..5, centre, strength, Mach), per-instance dt at CFL 0.5, all advanced
     together by CUDA-graph replay after the volume tiles are autotuned."""
@@ -316,7 +351,18 @@ def measure_batch(precision, steps, warmup, count=256):
            "graph_launches_per_step": 1, "gamma_range": [float(g.min()), float(g.max())],
            "degrees": {str(p): sum(1 for d in params if d["p"] == p) for p in range(2, 6)},
            "no_root_flagged": bool(st0 == -4 or st1 == -4)}
+    states = None
+    if keep_states or ref_states is not None:
+        states = [b.get_state(i) for i in range(count)]
+    if ref_states is not None:
+        # same instances, initial states, dt and number of steps (warm-up + timed) as the FP64 run
+        out["error_vs_fp64"] = state_error(np.concatenate([st.reshape(5, -1) for st in states], axis=1),
+                                           np.concatenate([st.reshape(5, -1) for st in ref_states], axis=1))
+        out["error_vs_fp64"]["steps"] = warmup + steps
+        out["error_vs_fp64"]["reference"] = "FP64 batch, same instances, states, dt and steps"
     b.close()
+    if keep_states:
+        return out, states
     return out
 
 
@@ -530,15 +576,19 @@ def run_full(args, rank, world, local_rank):
             p2 = kernel_profile(r2, 20)
             r2["solver"].close()
             t2 = sum(v[0] for v in p2.values())
+            err = error_vs_fp64(w2) if w2["precision"] != 0 else None
             forms[name] = {"value": r2["nodes"] * STAGES * steps2 / (r2["ms"] / 1e3),
                            "ms_per_step": r2["ms"] / steps2, "steps": steps2,
                            "gamma_range": [r2["gamma_min"], r2["gamma_max"]], "launches": int(r2["launches"]),
                            "kernel_share": {k: round(v[0] / t2, 4) for k, v in p2.items() if v[1] > 0},
                            "speedup_vs_fp64_same_physics": None}
+            if err is not None:
+                forms[name]["error_vs_fp64"] = err
             del r2
-        for prec, name in [(0, "batched_vortex_256_fp64"), (1, "batched_vortex_256_mixed"),
-                           (2, "batched_vortex_256_fp64x")]:
-            forms[name] = measure_batch(prec, 20, 3)
+        forms["batched_vortex_256_fp64"], ref = measure_batch(0, 20, 3, keep_states=True)
+        for prec, name in [(1, "batched_vortex_256_mixed"), (2, "batched_vortex_256_fp64x")]:
+            forms[name] = measure_batch(prec, 20, 3, ref_states=ref)
+        del ref
         fp = {"tgv_euler_p3_32^3_mixed": value, "tgv_euler_p3_32^3_fp64x": value,
               "tgv_ns_re1600_p4_32^3_fp64x": forms["tgv_ns_re1600_p4_32^3_fp64"]["value"],
               "tgv_ns_re1600_p4_32^3_mixed_noise": forms["tgv_ns_re1600_p4_32^3_fp64"]["value"],
