@@ -66,7 +66,9 @@ typedef struct {
   double mu;            /* dynamic viscosity; 0 = Euler (no viscous terms) */
   double Pr;            /* Prandtl number (mu > 0) */
   double R;             /* gas constant, p = rho R T */
-  int interface_diss;   /* 0: entropy-conservative SAT^I; 1: + Rusanov diss^I */
+  int interface_diss;   /* 0: entropy-conservative SAT^I; 1: + Rusanov diss^I;
+                           2: + matrix diss^I in entropy variables,
+                           (1/2) R |Lambda| T R^T [[w]] (Barth-scaled eigenvectors) */
   int relax;            /* ES_RELAX_* */
   int rk;               /* ES_RK_* */
   int precision;        /* ES_FP64, ES_MIXED or ES_FP64X */

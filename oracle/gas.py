@@ -19,7 +19,13 @@ these formulas):
   u = f^2, F = 1 + u/3 + u^2/5 + u^3/7 when u < eps_s else ln(zeta)/(2f), and
   a_ln = (aL + aR)/(2F).  eps_s = 1e-4 in FP64 (truncation below 1.2e-17).
 * Interface dissipation diss^I: scalar Rusanov (local Lax--Friedrichs) in
-  conserved variables with lambda = max over both sides of |v.n| + c.
+  conserved variables with lambda = max over both sides of |v.n| + c (diss = 1),
+  or the matrix dissipation in entropy variables of the references the paper cites
+  for diss^I (diss = 2): (1/2) R |Lambda| T R^T [[w]] with the eigenvectors R of
+  the flux Jacobian along the face normal and Barth's scaling T (R T R^T = dq/dw),
+  evaluated at the mean state rho = zb1 zb5, u = zb_v/zb1, p = zb5/zb1 of the
+  parameter-vector averages (any positive mean state keeps the term dissipative;
+  this one needs no logarithmic mean).
 * Viscous flux: Stokes stress with constant mu, Fourier heat flux with
   kappa = mu c_p / Pr, c_p = gamma R / (gamma - 1).  The flux is evaluated from
   the entropy-variable gradients theta_j = dw/dx_j through the chain rule
@@ -126,14 +132,45 @@ def ec_flux(qL, qR, g, m):
     return f
 
 
-def interface_flux(qL, qR, g, m, diss):
-    """Numerical interface flux f*(qL, qR) - diss * lambda/2 (qR - qL).
+def matrix_dissipation_parts(zL, zR, g, m):
+    """Eigenvectors R (5 x 5 x ...: R[:, k] the k-th), eigenvalues lam and Barth's
+    scaling T along direction m at the mean state of the parameter-vector averages."""
+    zb = 0.5 * (zL + zR)
+    rho = zb[0] * zb[4]
+    u = zb[1:4] / zb[0]
+    p = zb[4] / zb[0]
+    a = np.sqrt(g * p / rho)
+    h = a * a / (g - 1.0) + 0.5 * np.sum(u * u, axis=0)
+    un = u[m]
+    e = np.zeros((3,) + np.shape(un))
+    e[m] = 1.0
+    t1, t2 = [k for k in range(3) if k != m]
+    one, zero = np.ones_like(un), np.zeros_like(un)
+    R = np.empty((5, 5) + np.shape(un))
+    R[:, 0] = np.concatenate([[one], u - a * e, [h - un * a]])
+    R[:, 1] = np.concatenate([[one], u, [0.5 * np.sum(u * u, axis=0)]])
+    for col, t in ((2, t1), (3, t2)):
+        et = np.zeros((3,) + np.shape(un))
+        et[t] = 1.0
+        R[:, col] = np.concatenate([[zero], et, [u[t]]])
+    R[:, 4] = np.concatenate([[one], u + a * e, [h + un * a]])
+    lam = np.stack([un - a, un, un, un, un + a])
+    T = np.stack([rho / (2.0 * g), rho * (g - 1.0) / g, p, p, rho / (2.0 * g)])
+    return R, lam, T
 
-    qL is the state on the -x_m side, qR on the +x_m side of the face.
-    diss = 0 gives the entropy-conservative SAT, diss = 1 the Rusanov
-    entropy-stable one.
+
+def interface_flux(qL, qR, g, m, diss):
+    """Numerical interface flux f_num(qL, qR) (qL on the -x_m side, qR on the +x_m side).
+
+    diss = 0: the entropy-conservative flux; diss = 1: minus the Rusanov term
+    lambda/2 (qR - qL); diss = 2: minus the matrix term (1/2) R |Lambda| T R^T [[w]].
     """
     f = ec_flux(qL, qR, g, m)
+    if diss == 2:
+        R, lam, T = matrix_dissipation_parts(parameter_vector(qL, g), parameter_vector(qR, g), g, m)
+        jw = entropy_variables(qR, g) - entropy_variables(qL, g)
+        alpha = np.einsum("ik...,i...->k...", R, jw) * np.abs(lam) * T
+        return f - 0.5 * np.einsum("ik...,k...->i...", R, alpha)
     if diss:
         _, vL, _ = primitives(qL, g)
         _, vR, _ = primitives(qR, g)

@@ -124,7 +124,7 @@ int validate_config(const es_config& C) {
   if (C.rk != ES_RK_BS3 && C.rk != ES_RK_RK4) return ES_ERR_INVALID;
   if (C.precision != ES_FP64 && C.precision != ES_MIXED && C.precision != ES_FP64X) return ES_ERR_INVALID;
   if (C.relax != ES_RELAX_NONE && C.relax != ES_RELAX_LOCAL && C.relax != ES_RELAX_GLOBAL) return ES_ERR_INVALID;
-  if (C.interface_diss != 0 && C.interface_diss != 1) return ES_ERR_INVALID;
+  if (C.interface_diss < 0 || C.interface_diss > 2) return ES_ERR_INVALID;
   for (int m = 0; m < 3; ++m)
     if (!(C.hi[m] > C.lo[m])) return ES_ERR_INVALID;
   const long long K = (long long)C.nx * C.ny * C.nz;

@@ -362,12 +362,84 @@ __device__ __forceinline__ Zstate<TF> load_z(const TF* __restrict__ aux, long lo
   return s;
 }
 
+// Matrix interface dissipation in entropy variables (interface_diss = 2):
+// f -= (1/2) R |Lambda| T R^T [[w]] along x_m with the eigenvectors
+//   r1 = (1, u - a e_m, h - u_m a), r2 = (1, u, |u|^2/2), r3, r4 = (0, e_t, u_t) for
+//   the two tangential directions t, r5 = (1, u + a e_m, h + u_m a),
+// eigenvalues u_m - a, u_m (three times), u_m + a, and Barth's scaling
+// T = diag(rho/(2 gam), rho (gam-1)/gam, p, p, rho/(2 gam)) (R T R^T = dq/dw), all at
+// the mean state rho = zb1 zb5, u = zb_v/zb1, p = zb5/zb1 (a = sqrt(gam)/zb1,
+// h = a^2/(gam-1) + |u|^2/2) of the parameter-vector averages zb.  The entropy-variable
+// jump from the parameter vectors: [[w_v]] = [[z1 z_v]], [[w5]] = -[[z1^2]],
+// [[w1]] = -[[s]]/(gam-1) - [[|z_v|^2]]/2, [[s]] = -(gam+1) ln(z1R/z1L) - (gam-1) ln(z5R/z5L).
+template <typename TF>
+__device__ __forceinline__ TF tf_log(TF x) { return log(x); }
+template <>
+__device__ __forceinline__ float tf_log<float>(float x) { return logf(x); }
+
+template <typename TF>
+__device__ __forceinline__ void matrix_dissipation(const Zstate<TF>& L, const Zstate<TF>& R, int m,
+                                                   const FluxConst<TF>& C, TF f[5]) {
+  TF zb[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) zb[c] = TF(0.5) * (L.z[c] + R.z[c]);
+  const TF iz1 = fast_rcp(zb[0]);
+  const TF rho = zb[0] * zb[4];
+  const TF p = zb[4] * iz1;
+  const TF u[3] = {zb[1] * iz1, zb[2] * iz1, zb[3] * iz1};
+  const TF a = C.sqrt_gam * iz1;
+  const TF u2h = TF(0.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const TF h = a * a * C.inv_gm1 + u2h;
+  const TF un = u[m];
+  const int t1 = m == 0 ? 1 : 0, t2 = m == 2 ? 1 : 2;
+  // entropy-variable jump
+  const TF ds = -(C.gam + TF(1)) * tf_log(R.z[0] * fast_rcp(L.z[0])) - C.gm1 * tf_log(R.z[4] * fast_rcp(L.z[4]));
+  TF jw[5];
+  jw[0] = -(ds * C.inv_gm1) -
+          TF(0.5) * ((R.z[1] * R.z[1] + R.z[2] * R.z[2] + R.z[3] * R.z[3]) -
+                     (L.z[1] * L.z[1] + L.z[2] * L.z[2] + L.z[3] * L.z[3]));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) jw[1 + k] = R.z[0] * R.z[1 + k] - L.z[0] * L.z[1 + k];
+  jw[4] = -(R.z[0] * R.z[0] - L.z[0] * L.z[0]);
+  // characteristic amplitudes R^T [[w]], scaled by |lambda| T
+  const TF jwm = m == 0 ? jw[1] : (m == 1 ? jw[2] : jw[3]);
+  const TF jwt1 = t1 == 0 ? jw[1] : (t1 == 1 ? jw[2] : jw[3]);
+  const TF jwt2 = t2 == 1 ? jw[2] : jw[3];
+  const TF ut1 = t1 == 0 ? u[0] : (t1 == 1 ? u[1] : u[2]);
+  const TF ut2 = t2 == 1 ? u[1] : u[2];
+  const TF base = jw[0] + (u[0] * jw[1] + u[1] * jw[2] + u[2] * jw[3]);
+  const TF s_ac = rho * TF(0.5) * fast_rcp(C.gam);
+  TF a1 = (base - a * jwm + (h - un * a) * jw[4]) * (fabs(un - a) * s_ac);
+  TF a2 = (base + u2h * jw[4]) * (fabs(un) * rho * C.gm1 * fast_rcp(C.gam));
+  TF a3 = (jwt1 + ut1 * jw[4]) * (fabs(un) * p);
+  TF a4 = (jwt2 + ut2 * jw[4]) * (fabs(un) * p);
+  TF a5 = (base + a * jwm + (h + un * a) * jw[4]) * (fabs(un + a) * s_ac);
+  // D = sum_k a_k r_k
+  TF D[5];
+  D[0] = a1 + a2 + a5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) D[1 + k] = (a1 + a2 + a5) * u[k];
+  // the +-a e_m parts and the tangential vectors
+  if (m == 0) D[1] += a * (a5 - a1);
+  else if (m == 1) D[2] += a * (a5 - a1);
+  else D[3] += a * (a5 - a1);
+  if (t1 == 0) D[1] += a3;
+  else D[2] += a3;
+  if (t2 == 1) D[2] += a4;
+  else D[3] += a4;
+  D[4] = (a1 + a5) * h + un * a * (a5 - a1) + a2 * u2h + a3 * ut1 + a4 * ut2;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) f[v] -= TF(0.5) * D[v];
+}
+
 // interface flux f_num(L, R) of the EC flux with optional Rusanov dissipation
 template <typename TF>
 __device__ __forceinline__ void face_flux(const Zstate<TF>& L, TF izL, const Zstate<TF>& R, TF izR, int m,
                                           const FluxConst<TF>& C, int diss, TF f[5]) {
   ec_flux(L, R, m, C, f);
-  if (diss) {
+  if (diss == 2) {
+    matrix_dissipation(L, R, m, C, f);
+  } else if (diss) {
     TF qL[5], qR[5], lL, lR;
     z_to_q(L, izL, C, qL, lL, m);
     z_to_q(R, izR, C, qR, lR, m);

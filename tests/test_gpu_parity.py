@@ -470,3 +470,26 @@ def test_reciprocal_matches_ieee_division():
     ref = 1.0 / x
     ulp = np.abs(out.cpu().numpy().view(np.int64) - ref.view(np.int64))
     assert ulp.max() <= 1, ulp.max()
+
+
+# ---------------------------------------------------------------------------------------
+# matrix interface dissipation in entropy variables (interface_diss = 2)
+
+@pytest.mark.parametrize("p,n,mu,prec", [(2, (3, 5, 4), 0.0, 0), (3, (3, 4, 5), 0.02, 0), (4, (2, 3, 3), 0.0, 0),
+                                        (5, (2, 2, 3), 0.01, 0), (3, (3, 4, 5), 0.02, 2)])
+def test_rhs_matrix_dissipation(p, n, mu, prec):
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.5, 2.0)
+    mesh = dg.Mesh(p, n, lo, hi)
+    U = random_state(mesh, seed=p * 7 + n[0])
+    phys = dg.Physics(G, mu=mu, Pr=0.72, diss=2)
+    ref = dg.rhs(mesh, U, phys)
+    s = solver(p, n, lo, hi, mu=mu, interface_diss=2, precision=prec)
+    dq = s.rhs(s.to_device(U)).cpu().numpy()
+    assert s.status() == 0
+    assert_rhs_close(dq, ref, dg.rhs_term_magnitude(mesh, U, phys), eps=EPS if prec == 0 else 2.0 ** -47)
+    s.close()
+
+
+def test_advance_matrix_dissipation():
+    mesh, U, lo, hi = vortex_setup(N=4, p=3, nz=2)
+    compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=2), "BS3", 10)

@@ -114,17 +114,19 @@ def test_shock_advance_parity(prec, tab):
     s.close()
 
 
-@pytest.mark.parametrize("p,tab,rate_min", [(2, "BS3", 2.5), (3, "RK4", 3.5)])
-def test_viscous_shock_convergence(p, tab, rate_min):
+@pytest.mark.parametrize("p,tab,rate_min,diss", [(2, "BS3", 2.5, 1), (3, "RK4", 3.5, 1), (2, "BS3", 2.75, 2)])
+def test_viscous_shock_convergence(p, tab, rate_min, diss):
     """Table 2's study at N = 10, 15, 20 to t = 0.5 with U dt/dx^2 fixed: least-squares L2
     density rate above p + 1/2 (the paper observes 3.1 for p = 2, 3.4-4.0 for p = 3; at
     N = 5 both are pre-asymptotic).  The errors are of the size Table 2 lists (p = 3,
-    N = 20: 1.8e-5 here, 1.05e-5 there)."""
+    N = 20: 1.8e-5 here, 1.05e-5 there).  With the matrix interface dissipation
+    (diss = 2) the p = 2 rate is the paper's (2.9-3.0 here, 3.1 there; 2.6 with Rusanov)."""
     B = _B()
     errs = []
     Ns = (10, 15, 20)
     for n in Ns:
         mesh, phys, prm, lo, hi = shock_setup(p, n)
+        phys = dg.Physics(G, mu=prm["mu"], Pr=prm["prandtl"], diss=diss)
         x, _, _ = mesh.coords()
         U = inputs.viscous_shock_state(x, 0.0, prm)
         dt = 0.03 / n ** 2

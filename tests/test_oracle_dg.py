@@ -42,7 +42,7 @@ MESHES = [(2, (3, 2, 2)), (3, (2, 3, 2)), (4, (2, 2, 3))]
 
 
 @pytest.mark.parametrize("p,n", MESHES)
-@pytest.mark.parametrize("mu,diss", [(0.0, 0), (0.0, 1), (0.01, 1)])
+@pytest.mark.parametrize("mu,diss", [(0.0, 0), (0.0, 1), (0.01, 1), (0.0, 2)])
 def test_free_stream(p, n, mu, diss):
     mesh = dg.Mesh(p, n, (0, 0, 0), (1.0, 2.0, 1.5))
     U = np.empty(mesh.shape)
@@ -53,7 +53,7 @@ def test_free_stream(p, n, mu, diss):
 
 
 @pytest.mark.parametrize("p,n", MESHES)
-@pytest.mark.parametrize("mu,diss", [(0.0, 0), (0.0, 1), (0.02, 1)])
+@pytest.mark.parametrize("mu,diss", [(0.0, 0), (0.0, 1), (0.02, 1), (0.02, 2)])
 def test_conservation(p, n, mu, diss):
     mesh = dg.Mesh(p, n, (0, 0, 0), (1.0, 2.0, 1.5))
     U = smooth_state(mesh, seed=p, noise=0.05)
@@ -75,6 +75,10 @@ def test_entropy_conservation_ec(p, n):
     # with Rusanov interface dissipation the total entropy decreases
     R1 = dg.rhs(mesh, U, dg.Physics(G, diss=1))
     assert np.sum(mesh.element_sum(np.sum(W * R1, axis=0))) < -1e-6 * scale
+    # matrix interface dissipation: decreases too, by less than the scalar Rusanov term
+    R2 = dg.rhs(mesh, U, dg.Physics(G, diss=2))
+    d2 = np.sum(mesh.element_sum(np.sum(W * R2, axis=0)))
+    assert -np.sum(mesh.element_sum(np.sum(W * R1, axis=0))) > -d2 > 1e-8 * scale
 
 
 @pytest.mark.parametrize("p,n", MESHES)

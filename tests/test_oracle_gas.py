@@ -123,6 +123,46 @@ def test_rusanov_dissipates_entropy():
         assert np.all(np.sum(dw * (f_es - f_ec), axis=0) <= 1e-14)
 
 
+def _jacobian(fun, x, h=1e-6):
+    """Central-difference Jacobian of a vector function of a 5-vector."""
+    J = np.empty((5, 5))
+    for j in range(5):
+        dx = np.zeros(5)
+        dx[j] = h * max(1.0, abs(x[j]))
+        J[:, j] = (fun(x + dx) - fun(x - dx)) / (2 * dx[j])
+    return J
+
+
+@pytest.mark.parametrize("m", [0, 1, 2])
+def test_matrix_dissipation_eigensystem(m):
+    """At a single state the mean state is that state: R diag(lam) R^-1 is the flux
+    Jacobian df_m/dq and R T R^T = dq/dw (Barth's scaling for S = -rho s/(gamma-1));
+    a wrong eigenvector, eigenvalue or scale fails one of the two."""
+    q = rand_states(3, 21 + m)[:, 1]
+    z = gas.parameter_vector(q, G)
+    R, lam, T = gas.matrix_dissipation_parts(z, z, G, m)
+    A = _jacobian(lambda x: gas.euler_flux(x, G, m), q)
+    assert np.allclose(R @ np.diag(lam) @ np.linalg.inv(R), A, rtol=1e-7, atol=1e-7 * np.max(np.abs(A)))
+    dwdq = _jacobian(lambda x: gas.entropy_variables(x, G), q)
+    dqdw = np.linalg.inv(dwdq)
+    assert np.allclose(R @ np.diag(T) @ R.T, dqdw, rtol=1e-6, atol=1e-7 * np.max(np.abs(dqdw)))
+
+
+def test_matrix_dissipation_consistent_and_dissipative():
+    qL = rand_states(300, 16)
+    qR = rand_states(300, 17)
+    for m in range(3):
+        f_ec = gas.interface_flux(qL, qR, G, m, 0)
+        f_md = gas.interface_flux(qL, qR, G, m, 2)
+        dw = gas.entropy_variables(qR, G) - gas.entropy_variables(qL, G)
+        assert np.all(np.sum(dw * (f_md - f_ec), axis=0) <= 1e-14)
+        assert np.allclose(gas.interface_flux(qL, qL, G, m, 2), gas.euler_flux(qL, G, m), rtol=1e-13, atol=1e-13)
+        # the matrix form dissipates no more than the scalar one on each wave family:
+        # |lambda_k| <= lambda_max, so its entropy production is smaller in size
+        f_rs = gas.interface_flux(qL, qR, G, m, 1)
+        assert np.all(np.sum(dw * (f_md - f_ec), axis=0) >= np.sum(dw * (f_rs - f_ec), axis=0) - 1e-12)
+
+
 def test_viscous_flux_shear_and_positivity():
     # linear shear u = a y: tau_xy = mu a; heat flux from a temperature gradient
     rho, p = 1.2, 0.9
