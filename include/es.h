@@ -184,6 +184,8 @@ int es_profile_read(es_ctx* ctx, double* ms, long long* launches);
  * memory).  The paper has no counterpart; it is the same operation as es_rhs
  * (same kernels, same results) with the caller passing only inputs and
  * outputs: q and dqdt (device, [5][K][Np]) and optionally E_elem (device, [K]).
+ * A config describes a periodic mesh: boundaries set with es_set_boundary
+ * belong to a context and do not apply here.
  *
  * It allocates nothing: the kernels' scratch is one fixed array of
  * ES_NOALLOC_SCRATCH_BYTES (32 MiB) of device memory compiled into the
