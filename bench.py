@@ -366,6 +366,42 @@ def measure_batch(precision, steps, warmup, count=256, ref_states=None, keep_sta
     return out
 
 
+def measure_shock(precision, steps=50, warmup=3, n=25, p=3):
+    """Section 4.1.2 form: the moving viscous shock on n^3 elements of [-0.5, 0.5]^3 (M 2.5,
+    Re 10, Pr 3/4), Dirichlet-penalty boundaries on the x1 faces (exterior state evaluated on
+    the device at every stage time), RK(4,4), dt = 0.03 h^2; CUDA events around `steps` steps,
+    and the density error against the exact solution at the end."""
+    import torch
+    from paper_2003_08831_gb300 import inputs, _binding as B
+    from paper_2003_08831_gb300.solver import Solver
+    prm = inputs.viscous_shock_parameters(2.5, 10.0, 0.75)
+    s = Solver(p, (n, n, n), (-0.5,) * 3, (0.5,) * 3, mu=prm["mu"], Pr=0.75, rk=B.ES_RK_RK4, precision=precision)
+    s.set_boundary(0, B.ES_BC_VISCOUS_SHOCK, [2.5, 10.0, 0.75, -1.0])
+    xyz = s.coords()
+    q = s.to_device(inputs.viscous_shock_state(xyz[0], 0.0, prm))
+    dt = 0.03 / n ** 2
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s.advance(q, warmup, dt, t, want_hist=False, want_gamma_elem=False)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.advance(q, steps, dt, t, want_hist=False, want_gamma_elem=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if s.status() != 0:
+        raise RuntimeError("device status %d in the viscous-shock form" % s.status())
+    err = q.cpu().numpy().reshape(5, -1)[0] - inputs.viscous_shock_state(xyz[0], t.item(), prm)[0].reshape(-1)
+    nodes = s.N
+    s.close()
+    return {"value": nodes * 4 * steps / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps, "nodes": int(nodes),
+            "elements": n ** 3, "p": p, "rk": "RK(4,4) (4 stages)", "boundaries": "Dirichlet penalty on x1 (exact solution)",
+            "t_end": t.item(), "density_rel_l2_error_vs_exact": float(np.linalg.norm(err) / np.linalg.norm(
+                inputs.viscous_shock_state(xyz[0], t.item(), prm)[0]))}
+
+
 def kernel_roofline(p, n_el, wl, prof, peak, vol_flops):
     """Per kernel kind: algorithmic flops per launch / average event-timed launch, as a
     fraction of the ALU peak (FP64 workloads; other precisions report null)."""
@@ -585,6 +621,8 @@ def run_full(args, rank, world, local_rank):
             if err is not None:
                 forms[name]["error_vs_fp64"] = err
             del r2
+        forms["viscous_shock_ns_p3_25^3_fp64"] = measure_shock(0)
+        forms["viscous_shock_ns_p3_25^3_fp64x"] = measure_shock(2)
         forms["batched_vortex_256_fp64"], ref = measure_batch(0, 20, 3, keep_states=True)
         for prec, name in [(1, "batched_vortex_256_mixed"), (2, "batched_vortex_256_fp64x")]:
             forms[name] = measure_batch(prec, 20, 3, ref_states=ref)
@@ -593,7 +631,8 @@ def run_full(args, rank, world, local_rank):
               "tgv_ns_re1600_p4_32^3_fp64x": forms["tgv_ns_re1600_p4_32^3_fp64"]["value"],
               "tgv_ns_re1600_p4_32^3_mixed_noise": forms["tgv_ns_re1600_p4_32^3_fp64"]["value"],
               "batched_vortex_256_mixed": forms["batched_vortex_256_fp64"]["value"],
-              "batched_vortex_256_fp64x": forms["batched_vortex_256_fp64"]["value"]}
+              "batched_vortex_256_fp64x": forms["batched_vortex_256_fp64"]["value"],
+              "viscous_shock_ns_p3_25^3_fp64x": forms["viscous_shock_ns_p3_25^3_fp64"]["value"]}
         for k, base in fp.items():
             forms[k]["speedup_vs_fp64_same_physics"] = forms[k]["value"] / base
         for k in forms:
