@@ -41,17 +41,23 @@ WORKLOADS = {
     "tgv_euler_p3_32^3_fp64": dict(p=3, n=32, mu=0.0, precision=0, ic="tgv", steps=200),
     "tgv_euler_p3_32^3_mixed": dict(p=3, n=32, mu=0.0, precision=1, ic="tgv", steps=200),
     "tgv_euler_p3_32^3_fp64x": dict(p=3, n=32, mu=0.0, precision=2, ic="tgv", steps=200),
+    "tgv_euler_p3_32^3_mixed_ff": dict(p=3, n=32, mu=0.0, precision=3, ic="tgv", steps=200),
     "tgv_ns_re1600_p4_32^3_fp64x": dict(p=4, n=32, mu=1.0 / 1600.0, precision=2, ic="tgv", steps=200),
     "tgv_ns_re1600_p4_32^3_fp64": dict(p=4, n=32, mu=1.0 / 1600.0, precision=0, ic="tgv", steps=200),
     "tgv_ns_re1600_p4_32^3_mixed_noise": dict(p=4, n=32, mu=1.0 / 1600.0, precision=1, ic="tgv_noise", steps=200),
+    "tgv_ns_re1600_p4_32^3_mixed_ff_noise": dict(p=4, n=32, mu=1.0 / 1600.0, precision=3, ic="tgv_noise",
+                                                 steps=200),
     "vortex_euler_p3_4^3_fp64": dict(p=3, n=4, mu=0.0, precision=0, ic="vortex", steps=20),
 }
 MAIN = "tgv_euler_p3_32^3_fp64"
 PRECISION_LABEL = {0: "FP64",
-                   1: "mixed (FP32 fluxes, FP64 state/estimate/gamma)",
+                   1: "mixed (FP32 fluxes/SATs/viscous terms; FP64 state, stage states, entropy increments, "
+                      "estimate sums and gamma solve)",
                    2: "FP64X (float-float fluxes/SATs/viscous terms on the FP32 pipe, ~2^-47 per operation; "
-                      "FP64 state/estimate/gamma)"}
-DTYPE = {0: "f64", 1: "f64+f32", 2: "f64+f32x2"}
+                      "FP64 state/estimate/gamma)",
+                   3: "mixed float-float (FP32 fluxes/SATs/viscous terms; stage states, entropy increments, "
+                      "estimate sums and gamma solve in float-float on the FP32 pipe; FP64 state)"}
+DTYPE = {0: "f64", 1: "f64+f32", 2: "f64+f32x2", 3: "f64+f32+f32x2"}
 STAGES = 3  # BS3: b_4 = 0
 
 
@@ -604,8 +610,9 @@ def run_full(args, rank, world, local_rank):
     out["e2e"] = measure_e2e(wl, min(args.steps, 20), 3)
     if world == 1 and not args.no_forms:
         forms = {}
-        for name in ["tgv_euler_p3_32^3_mixed", "tgv_euler_p3_32^3_fp64x", "tgv_ns_re1600_p4_32^3_fp64",
-                     "tgv_ns_re1600_p4_32^3_fp64x", "tgv_ns_re1600_p4_32^3_mixed_noise"]:
+        for name in ["tgv_euler_p3_32^3_mixed", "tgv_euler_p3_32^3_mixed_ff", "tgv_euler_p3_32^3_fp64x",
+                     "tgv_ns_re1600_p4_32^3_fp64", "tgv_ns_re1600_p4_32^3_fp64x",
+                     "tgv_ns_re1600_p4_32^3_mixed_noise", "tgv_ns_re1600_p4_32^3_mixed_ff_noise"]:
             w2 = WORKLOADS[name]
             steps2 = 50
             r2 = measure_device(w2, steps2, 3)
@@ -624,13 +631,17 @@ def run_full(args, rank, world, local_rank):
         forms["viscous_shock_ns_p3_25^3_fp64"] = measure_shock(0)
         forms["viscous_shock_ns_p3_25^3_fp64x"] = measure_shock(2)
         forms["batched_vortex_256_fp64"], ref = measure_batch(0, 20, 3, keep_states=True)
-        for prec, name in [(1, "batched_vortex_256_mixed"), (2, "batched_vortex_256_fp64x")]:
+        for prec, name in [(1, "batched_vortex_256_mixed"), (3, "batched_vortex_256_mixed_ff"),
+                           (2, "batched_vortex_256_fp64x")]:
             forms[name] = measure_batch(prec, 20, 3, ref_states=ref)
         del ref
-        fp = {"tgv_euler_p3_32^3_mixed": value, "tgv_euler_p3_32^3_fp64x": value,
+        fp = {"tgv_euler_p3_32^3_mixed": value, "tgv_euler_p3_32^3_mixed_ff": value,
+              "tgv_euler_p3_32^3_fp64x": value,
               "tgv_ns_re1600_p4_32^3_fp64x": forms["tgv_ns_re1600_p4_32^3_fp64"]["value"],
               "tgv_ns_re1600_p4_32^3_mixed_noise": forms["tgv_ns_re1600_p4_32^3_fp64"]["value"],
+              "tgv_ns_re1600_p4_32^3_mixed_ff_noise": forms["tgv_ns_re1600_p4_32^3_fp64"]["value"],
               "batched_vortex_256_mixed": forms["batched_vortex_256_fp64"]["value"],
+              "batched_vortex_256_mixed_ff": forms["batched_vortex_256_fp64"]["value"],
               "batched_vortex_256_fp64x": forms["batched_vortex_256_fp64"]["value"],
               "viscous_shock_ns_p3_25^3_fp64x": forms["viscous_shock_ns_p3_25^3_fp64"]["value"]}
         for k, base in fp.items():

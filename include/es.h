@@ -45,11 +45,15 @@ extern "C" {
 #define ES_RK_RK4 1 /* classical RK(4,4) */
 
 #define ES_FP64 0  /* every operation in FP64 */
-#define ES_MIXED 1 /* FP32 fluxes/SATs/viscous terms; FP64 state, entropy sums, gamma solve */
+#define ES_MIXED 1 /* FP32 fluxes/SATs/viscous terms; FP64 state, stage states,
+                      entropy-variable increments, entropy sums and gamma solve */
 #define ES_FP64X 2 /* fluxes/SATs/viscous terms in float-float arithmetic on the FP32 pipe
                       (hi + lo pairs of floats, ~2^-47 relative per operation, FP32 exponent
                       range); FP64 state, entropy sums and gamma solve.  es_rhs_noalloc
                       evaluates such a configuration with the FP64 kernels. */
+#define ES_MIXED_FF 3 /* FP32 fluxes/SATs/viscous terms as ES_MIXED; the stage states,
+                      entropy-variable increments, the per-element sums and the gamma
+                      solve in float-float on the FP32 pipe (FP64 state, FP64 gamma). */
 
 #define ES_RELAX_NONE 0  /* baseline RK, gamma = 1 */
 #define ES_RELAX_LOCAL 1 /* gamma = min_kappa gamma_kappa (Theorem 2.3) */
@@ -71,10 +75,11 @@ typedef struct {
                            (1/2) R |Lambda| T R^T [[w]] (Barth-scaled eigenvectors) */
   int relax;            /* ES_RELAX_* */
   int rk;               /* ES_RK_* */
-  int precision;        /* ES_FP64, ES_MIXED or ES_FP64X */
+  int precision;        /* ES_FP64, ES_MIXED, ES_FP64X or ES_MIXED_FF */
   double delta_floor;   /* elements whose RMS relative change over the step is
                            <= delta_floor are unconstrained (gamma_kappa = +inf);
-                           <= 0 selects 1e-8 (ES_FP64, ES_FP64X) or 4e-6 (ES_MIXED:
+                           <= 0 selects 1e-8 (ES_FP64, ES_FP64X) or 4e-6 (ES_MIXED,
+                           ES_MIXED_FF:
                            64 eps_32, above the FP32 right-hand side's rounding noise) */
 } es_config;
 

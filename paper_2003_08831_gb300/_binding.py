@@ -19,7 +19,7 @@ ES_ERR_NO_ROOT = -4
 ES_ERR_NOMEM = -6
 ES_ERR_TOO_LARGE = -7
 ES_RK_BS3, ES_RK_RK4 = 0, 1
-ES_FP64, ES_MIXED, ES_FP64X = 0, 1, 2
+ES_FP64, ES_MIXED, ES_FP64X, ES_MIXED_FF = 0, 1, 2, 3
 ES_RELAX_NONE, ES_RELAX_LOCAL, ES_RELAX_GLOBAL = 0, 1, 2
 ES_BC_PERIODIC, ES_BC_STATE, ES_BC_VISCOUS_SHOCK = 0, 1, 2
 

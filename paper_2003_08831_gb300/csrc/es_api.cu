@@ -122,7 +122,7 @@ int validate_config(const es_config& C) {
   if (C.p < 2 || C.p > 5 || C.nx < 1 || C.ny < 1 || C.nz < 1) return ES_ERR_INVALID;
   if (!(C.gamma_gas > 1.0) || !(C.R > 0.0) || C.mu < 0.0 || (C.mu > 0.0 && !(C.Pr > 0.0))) return ES_ERR_INVALID;
   if (C.rk != ES_RK_BS3 && C.rk != ES_RK_RK4) return ES_ERR_INVALID;
-  if (C.precision != ES_FP64 && C.precision != ES_MIXED && C.precision != ES_FP64X) return ES_ERR_INVALID;
+  if (C.precision < ES_FP64 || C.precision > ES_MIXED_FF) return ES_ERR_INVALID;
   if (C.relax != ES_RELAX_NONE && C.relax != ES_RELAX_LOCAL && C.relax != ES_RELAX_GLOBAL) return ES_ERR_INVALID;
   if (C.interface_diss < 0 || C.interface_diss > 2) return ES_ERR_INVALID;
   for (int m = 0; m < 3; ++m)
@@ -186,6 +186,7 @@ void build_params(const es_config& C, Params* out) {
   P.diss = C.interface_diss;
   P.p1 = P1;
   P.ninst = 1;
+  P.ff_est = (C.precision == ES_MIXED_FF || C.precision == ES_FP64X) ? 1 : 0;
   P.g0 = instance_geom(C, 0);
   P.geom = nullptr;
   P.elem_inst = nullptr;
@@ -420,7 +421,7 @@ int group_init(Group& g, const es_config* insts, int n, int stages, bool own_sta
   g.P1 = C.p + 1;
   g.Np = g.P1 * g.P1 * g.P1;
   g.ninst = n;
-  g.tf = C.precision == ES_MIXED ? 4 : 8;  // bytes per flux-precision value (float-float: 8)
+  g.tf = (C.precision == ES_MIXED || C.precision == ES_MIXED_FF) ? 4 : 8;  // bytes per flux value (float-float: 8)
   g.ffx = C.precision == ES_FP64X;
   build_params(C, &g.P);
   long long K = 0;
@@ -574,7 +575,7 @@ StageRelax relax_base(Engine& E, Group& g) {
   // 1e-8 leaves a wide margin; FP32 right-hand sides carry rounding noise of relative size
   // ~eps_32 times the flux-to-state cancellation, and below 64 eps_32 ~ 4e-6 an element's
   // relaxation would be fitted to that noise.
-  const double floor_default = g.cfg.precision == ES_MIXED ? 4e-6 : 1e-8;
+  const double floor_default = (g.cfg.precision == ES_MIXED || g.cfg.precision == ES_MIXED_FF) ? 4e-6 : 1e-8;
   sr.delta_floor = g.cfg.delta_floor > 0.0 ? g.cfg.delta_floor : floor_default;
   sr.gamma_max = 8.0;
   return sr;

@@ -68,6 +68,8 @@ struct Params {
   int diss;                    // Rusanov interface dissipation on/off
   int p1;                      // p + 1
   int ninst;                   // instances in the group
+  int ff_est;                  // FP32 fluxes: entropy increments, the relaxation sums and
+                               // the gamma solve in float-float (1) or in FP64 (0)
   InstGeom g0;                 // the instance when geom is null (single-instance context)
   const InstGeom* geom;        // device table [ninst] (batches), or null
   const int* elem_inst;        // device [K]: instance of each element (batches), or null

@@ -247,11 +247,13 @@ __device__ __forceinline__ bool relax_node_eval_ff(const RelaxNodeF& nd, ff g, c
 // ---------------------------------------------------------------------------
 // y = u (+ gamma d when the instance has a pending relaxed update and this is the
 // step's first stage) + dt sum_j a_ij k_j; NPREV stages enter (compile time).
-// FP64 mode: everything in FP64.  Mixed and ES_FP64X: the FP64 state is split into
-// float-float (integer pipe), the stage increment e = dt sum_j a_ij k_j, y = u + e,
-// the parameter vector and w(y) - w(u) are formed in float-float on the FP32 pipe
-// (the mixed mode rounds z to FP32 for its fluxes).
-template <typename TF, int NPREV>
+// FP64 mode, and the mixed mode with FP64 estimates (P.ff_est = 0): everything in
+// FP64 (the mixed mode reads FP32 k_j and rounds z to FP32 for its fluxes).  ES_FP64X
+// and the mixed float-float mode: the FP64 state is split into float-float (integer
+// pipe), the stage increment e = dt sum_j a_ij k_j, y = u + e, the parameter vector
+// and w(y) - w(u) are formed in float-float on the FP32 pipe.  FP64 selects the path
+// at compile time (the two differ widely in register use).
+template <typename TF, int NPREV, bool FP64>
 __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __restrict__ status) {
   const long long N = (long long)P.K * sp.Np;
   const double gam = P.gam;
@@ -268,7 +270,7 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
         sp.q[v * N + g] = u[v];
       }
     }
-    if constexpr (std::is_same<TF, double>::value) {
+    if constexpr (FP64) {
       double y[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) y[v] = u[v];
@@ -277,9 +279,9 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
 #pragma unroll
         for (int j = 0; j < NPREV; ++j) {
           const double c = sp.coef[j] * dt;
-          const double* kj = static_cast<const double*>(sp.k[j]);
+          const TF* kj = static_cast<const TF*>(sp.k[j]);
 #pragma unroll
-          for (int v = 0; v < 5; ++v) y[v] = fma(c, kj[v * N + g], y[v]);
+          for (int v = 0; v < 5; ++v) y[v] = fma(c, double(kj[v * N + g]), y[v]);
         }
       }
       const double rho = y[0];
@@ -290,12 +292,12 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
       // z1 = sqrt(rho/p) = rho / sqrt(rho p), z5 = sqrt(rho p)
       const double rs = rsqrt(rho * p);
       const double z1 = rho * rs;
-      aux[0 * N + g] = z1;
-      aux[1 * N + g] = z1 * v0;
-      aux[2 * N + g] = z1 * v1;
-      aux[3 * N + g] = z1 * v2;
-      aux[4 * N + g] = rho * p * rs;
-      aux[5 * N + g] = p * rs;  // 1/z1 = sqrt(p/rho)
+      aux[0 * N + g] = TF(z1);
+      aux[1 * N + g] = TF(z1 * v0);
+      aux[2 * N + g] = TF(z1 * v1);
+      aux[3 * N + g] = TF(z1 * v2);
+      aux[4 * N + g] = TF(rho * p * rs);
+      aux[5 * N + g] = TF(p * rs);  // 1/z1 = sqrt(p/rho)
       if (sp.dw) {
         double e[5], dw[5];
 #pragma unroll
@@ -602,9 +604,10 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
                                                    const TF* __restrict__ fV) {
   constexpr int P2 = P1 * P1, Np = P1 * P2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TF* za = reinterpret_cast<TF*>(smem_raw);            // [kAux][EPB*Np]
+  // the FP64 reduction rows first: they stay 8-byte aligned whatever EPB * Np and TF
+  double* red = reinterpret_cast<double*>(smem_raw);   // [2][EPB*Np]
+  TF* za = reinterpret_cast<TF*>(red + 2 * EPB * Np);  // [kAux][EPB*Np]
   TF* acc = za + kAux * EPB * Np;                       // [5][EPB*Np]
-  double* red = reinterpret_cast<double*>(acc + 5 * EPB * Np);  // [2][EPB*Np]
   const long long N = (long long)P.K * Np;
   const int e0 = blockIdx.x * EPB;
   const int nel = min(EPB, P.K - e0);
@@ -700,28 +703,34 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
   // node phase: write k_i (or, in the last stage, d = sum_j c_j k_j + c_self k_i), element sums
   const bool wantE = sv.E != nullptr;
   const bool wantA = sv.dw != nullptr;
+  // d and the element sums in FP64 (FP64 mode; mixed mode with FP64 estimates), else
+  // in float-float joined to FP64 once
+  const bool fp64_sums = std::is_same<TF, double>::value || (std::is_same<TF, float>::value && !P.ff_est);
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
     const long long g = (long long)e0 * Np + t;
     const int n = t % Np;
     const InstGeom& G = geom_of(P, inst_of(P, e0 + t / Np));
-    if constexpr (std::is_same<TF, double>::value) {
+    if (fp64_sums) {
       const double Pn = mass_weight<P1>(P, G.J, n);
       double k[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) k[v] = acc[v * EPB * Np + t];
+      for (int v = 0; v < 5; ++v) k[v] = double(acc[v * EPB * Np + t]);
       if (sv.d_out) {
         const double dt = G.dt;
-        const double* const* dk = reinterpret_cast<const double* const*>(sv.dk);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           double dv = (sv.dcoef_self * dt) * k[v];
-          for (int j = 0; j < sv.nd; ++j) dv = fma(sv.dcoef[j] * dt, dk[j][v * N + g], dv);
+          for (int j = 0; j < sv.nd; ++j)
+            dv = fma(sv.dcoef[j] * dt, double(static_cast<const TF*>(sv.dk[j])[v * N + g]), dv);
           sv.d_out[v * N + g] = dv;
         }
-      } else {
-        double* ko = sv.kout64 ? sv.kout64 : static_cast<double*>(sv.kout);
+      } else if (sv.kout64) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) ko[v * N + g] = k[v];
+        for (int v = 0; v < 5; ++v) sv.kout64[v * N + g] = k[v];
+      } else {
+        TF* ko = static_cast<TF*>(sv.kout);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ko[v * N + g] = acc[v * EPB * Np + t];
       }
       if (wantE) {
         Zstate<TF> s;
@@ -741,8 +750,8 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
         red[EPB * Np + t] = Pn * G.dt * sum;
       }
     } else {
-      // mixed / float-float: k stays in the flux precision; d and the element sums are
-      // formed in float-float and joined to FP64 once
+      // float-float estimates: k stays in the flux precision; d and the element sums
+      // are formed in float-float and joined to FP64 once
       TF kt[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) kt[v] = acc[v * EPB * Np + t];
@@ -794,12 +803,10 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
     double sE = 0.0, sA = 0.0;
     for (int n = lane; n < Np; n += 32) {
       if (wantE) sE += red[el * Np + n];
-      if constexpr (std::is_same<TF, double>::value) {
-        if (wantA) sA += red[EPB * Np + el * Np + n];
-      }
+      if (fp64_sums && wantA) sA += red[EPB * Np + el * Np + n];
     }
     if (wantE) sE = warp_sum(sE);
-    if constexpr (std::is_same<TF, double>::value) {
+    if (fp64_sums) {
       sA = warp_sum(sA);
     } else if (wantA) {
       ff s(0.0f, 0.0f);
@@ -1312,15 +1319,27 @@ __global__ void k_entropy(Params P, const double* __restrict__ q, double* __rest
 
 // ---------------------------------------------------------------------------
 // launchers
+template <typename TF, bool FP64>
+void prep_launch(const Params& P, const StagePrep& sp, TF* a, int* status, cudaStream_t st, int grid) {
+  switch (sp.nprev) {
+    case 0: k_prep<TF, 0, FP64><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+    case 1: k_prep<TF, 1, FP64><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+    case 2: k_prep<TF, 2, FP64><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+    default: k_prep<TF, 3, FP64><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+  }
+}
+
 template <int P1, typename TF>
 void Launcher<P1, TF>::prep(const Params& P, const StagePrep& sp, void* aux, int* status, cudaStream_t st,
                             int grid) {
   TF* a = static_cast<TF*>(aux);
-  switch (sp.nprev) {
-    case 0: k_prep<TF, 0><<<grid, 256, 0, st>>>(P, sp, a, status); break;
-    case 1: k_prep<TF, 1><<<grid, 256, 0, st>>>(P, sp, a, status); break;
-    case 2: k_prep<TF, 2><<<grid, 256, 0, st>>>(P, sp, a, status); break;
-    default: k_prep<TF, 3><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+  if constexpr (std::is_same<TF, double>::value) {
+    prep_launch<TF, true>(P, sp, a, status, st, grid);
+  } else if constexpr (std::is_same<TF, float>::value) {
+    if (P.ff_est) prep_launch<TF, false>(P, sp, a, status, st, grid);
+    else prep_launch<TF, true>(P, sp, a, status, st, grid);
+  } else {
+    prep_launch<TF, false>(P, sp, a, status, st, grid);
   }
 }
 
@@ -1388,11 +1407,12 @@ void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* a
 
 template <int P1, typename TF>
 void Launcher<P1, TF>::relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid) {
-  // the u_new entry point (es_relax_step) and the FP64 mode solve in FP64; 4 warps per
-  // block, RelaxGroup<P1>::EPW elements per warp
+  // the u_new entry point (es_relax_step), the FP64 mode and the mixed mode with FP64
+  // estimates solve in FP64; 4 warps per block, RelaxGroup<P1>::EPW elements per warp
   const int need = (P.K + 4 * RelaxGroup<P1>::EPW - 1) / (4 * RelaxGroup<P1>::EPW);
   const int g = grid < need ? grid : need;
-  if (sr.u_new || std::is_same<TF, double>::value) k_relax<P1><<<g, 128, 0, st>>>(P, sr);
+  if (sr.u_new || std::is_same<TF, double>::value || (std::is_same<TF, float>::value && !P.ff_est))
+    k_relax<P1><<<g, 128, 0, st>>>(P, sr);
   else k_relax_ff<P1><<<g, 128, 0, st>>>(P, sr);
 }
 

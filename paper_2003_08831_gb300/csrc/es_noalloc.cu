@@ -69,7 +69,7 @@ int setup_device(int dev) {
 
 extern "C" size_t es_rhs_noalloc_scratch_bytes(const es_config* cfg) {
   if (!cfg || validate_config(*cfg) != ES_OK) return 0;
-  const size_t tf = cfg->precision == ES_MIXED ? 4 : 8;
+  const size_t tf = (cfg->precision == ES_MIXED || cfg->precision == ES_MIXED_FF) ? 4 : 8;
   const size_t P1 = size_t(cfg->p) + 1;
   const size_t K = size_t(cfg->nx) * cfg->ny * cfg->nz;
   const size_t N = K * P1 * P1 * P1;
@@ -95,7 +95,7 @@ extern "C" int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqd
 
   Params P;
   build_params(*cfg, &P);
-  const bool fp64 = cfg->precision != ES_MIXED;
+  const bool fp64 = cfg->precision != ES_MIXED && cfg->precision != ES_MIXED_FF;
   const size_t tf = fp64 ? 8 : 4;
   const int P1 = cfg->p + 1;
   const long long K = (long long)cfg->nx * cfg->ny * cfg->nz;

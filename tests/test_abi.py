@@ -39,3 +39,15 @@ def test_strerror_and_invalid_config_without_gpu():
     cfg = _binding.make_config(3, (0, 2, 2))
     assert lib.es_create(ctypes.byref(cfg), ctypes.byref(ctx)) == _binding.ES_ERR_INVALID
     assert lib.es_create(None, ctypes.byref(ctx)) == _binding.ES_ERR_INVALID
+
+
+def test_binding_constants_match_header():
+    """Every integer constant the binding re-exports equals the header's #define, and
+    the configuration enums (status, RK, precision, relaxation, boundary) are all there."""
+    with open(os.path.join(ROOT, "include", "es.h")) as f:
+        defs = dict(re.findall(r"#define\s+(ES_\w+)\s+(-?\d+)\s", f.read()))
+    need = [k for k in defs if k.startswith(("ES_OK", "ES_ERR_", "ES_RK_", "ES_FP64", "ES_MIXED",
+                                              "ES_RELAX_", "ES_BC_"))]
+    assert {"ES_MIXED", "ES_MIXED_FF", "ES_FP64X"} <= set(need)
+    for k in need:
+        assert getattr(_binding, k) == int(defs[k]), k

@@ -47,9 +47,9 @@ def oracle_run(inst, nsteps):
     return mesh, U, dt, Uo, t, hist
 
 
-def build_batch(insts):
+def build_batch(insts, precision=0):
     from paper_2003_08831_gb300.solver import BatchSolver
-    b = BatchSolver(insts)
+    b = BatchSolver(insts, precision=precision)
     dts = []
     for i, inst in enumerate(insts):
         mesh = dg.Mesh(inst["p"], inst["n"], inst["lo"], inst["hi"])
@@ -79,6 +79,29 @@ def test_batch_against_oracle():
         assert np.all(err < TOL), (i, err)
         assert abs(t_gpu[i] - t) < TOL * t
         assert abs(g_gpu[i] - hist[-1].gamma) < 1e-10 * hist[-1].gamma
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [1, 3])
+def test_mixed_batch_against_oracle(precision):
+    """FP32 fluxes in a batch (ES_MIXED: FP64 estimates; ES_MIXED_FF: float-float
+    estimates): states and relaxed times t_gamma within 1e-5 relative of the FP64
+    oracle after 5 relaxed steps (the FP32 flux rounding moves each gamma by ~1e-7)."""
+    insts = instances(6)
+    nsteps = 5
+    b, dts = build_batch(insts, precision)
+    b.advance(nsteps)
+    assert b.status() == 0
+    t_gpu, _ = b.times()
+    for i, inst in enumerate(insts):
+        mesh, U, dt, Uo, t, hist = oracle_run(inst, nsteps)
+        q = b.get_state(i)
+        ref = Uo.reshape(5, -1)
+        nref = np.sqrt(np.sum(ref ** 2, axis=1))
+        nref = np.maximum(nref, 1e-3 * nref.max())     # the vortex has no x3 momentum
+        err = np.sqrt(np.sum((q.reshape(5, -1) - ref) ** 2, axis=1)) / nref
+        assert np.all(err < 1e-5), (i, err)
+        assert abs(t_gpu[i] - t) < 1e-5 * t, (i, t_gpu[i], t)
     b.close()
 
 

@@ -381,9 +381,11 @@ def test_mixed_rhs_error(p, n, mu):
     assert np.all(err <= np.maximum(bound, 1e-6)), (err, bound)
 
 
+@pytest.mark.parametrize("prec", [1, 3])
 @pytest.mark.parametrize("case", ["vortex", "tgv_noise_ns"])
-def test_mixed_advance_error(case):
-    """Mixed-precision relaxed steps against the FP64 oracle: state relative L2 <= 1e-5."""
+def test_mixed_advance_error(case, prec):
+    """Mixed-precision relaxed steps against the FP64 oracle, with FP64 (ES_MIXED) and
+    float-float (ES_MIXED_FF) estimates: state relative L2 <= 1e-5."""
     from paper_2003_08831_gb300 import _binding as B
     if case == "vortex":
         mesh, U, lo, hi = vortex_setup()
@@ -398,7 +400,7 @@ def test_mixed_advance_error(case):
         nsteps = 10
     dt = rk.stable_dt(mesh, U, phys, 0.5)
     Uo, to, hist = rk.advance(mesh, U, dt, nsteps, phys, rk.BS3)
-    s = solver(mesh.p, mesh.n, lo, hi, mu=phys.mu, precision=B.ES_MIXED)
+    s = solver(mesh.p, mesh.n, lo, hi, mu=phys.mu, precision=prec)
     q = s.to_device(U)
     t, gh, gk = s.advance(q, nsteps, dt)
     assert s.status() == 0

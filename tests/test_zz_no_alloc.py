@@ -30,7 +30,8 @@ def test_scratch_size_limit_is_checked_on_the_host():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("p,n,mu,precision", [(3, (5, 4, 3), 0.0, 0), (4, (3, 3, 4), 0.01, 0), (3, (4, 3, 5), 0.0, 1)])
+@pytest.mark.parametrize("p,n,mu,precision", [(3, (5, 4, 3), 0.0, 0), (4, (3, 3, 4), 0.01, 0), (3, (4, 3, 5), 0.0, 1),
+                                              (4, (3, 4, 3), 0.01, 3)])
 def test_rhs_noalloc_matches_es_rhs_on_two_calls(p, n, mu, precision):
     import torch
 
