@@ -89,6 +89,10 @@ __device__ __forceinline__ ff to_ff(ff x) { return x; }
 __device__ __forceinline__ ff to_ff(float x) { return ff(x, 0.0f); }
 __device__ __forceinline__ ff to_ff(double x) { return ff_from_double(x); }
 __device__ __forceinline__ ff ff_half(ff x) { return ff(0.5f * x.hi, 0.5f * x.lo); }
+// a float-float value in the flux precision (float: hi + lo rounded once)
+template <typename T> __device__ __forceinline__ T tf_from_ff(ff x);
+template <> __device__ __forceinline__ float tf_from_ff<float>(ff x) { return __fadd_rn(x.hi, x.lo); }
+template <> __device__ __forceinline__ ff tf_from_ff<ff>(ff x) { return x; }
 __device__ __forceinline__ ff ff_twice(ff x) { return ff(2.0f * x.hi, 2.0f * x.lo); }
 
 // log(1 + z) - z for |z| <= 1e-3: z^2 (-1/2 + z/3 + tail) with z^2, z/3 and the sum in
@@ -245,14 +249,40 @@ __device__ __forceinline__ bool relax_node_eval_ff(const RelaxNodeF& nd, ff g, c
 }
 
 // ---------------------------------------------------------------------------
+// the parameter vector z = (z1, z1 v, z5, 1/z1) of a float-float state y, with
+// z1 = sqrt(rho/p) = rho / sqrt(rho p), z5 = sqrt(rho p); false if rho or p <= 0
+__device__ __forceinline__ bool param_vector_ff(const ff y[5], const FluxConst<ff>& C, ff z[6]) {
+  const ff rho = y[0];
+  const ff ir = ff_rcp(rho);
+  const ff v0 = y[1] * ir, v1 = y[2] * ir, v2 = y[3] * ir;
+  const ff p = C.gm1 * (y[4] - ff_half(y[1] * v0 + y[2] * v1 + y[3] * v2));
+  const bool ok = rho.hi > 0.0f && p.hi > 0.0f;
+  const ff rs = ff_rsqrt(rho * p);
+  const ff z1 = rho * rs;
+  z[0] = z1;
+  z[1] = z1 * v0;
+  z[2] = z1 * v1;
+  z[3] = z1 * v2;
+  z[4] = rho * p * rs;
+  z[5] = p * rs;
+  return ok;
+}
+
+// FP64 value of a flux-precision value (float: the bits placed on the integer pipe)
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64_bits(x); }
+__device__ __forceinline__ double to_f64(ff x) { return double(x); }
+
+// ---------------------------------------------------------------------------
 // y = u (+ gamma d when the instance has a pending relaxed update and this is the
 // step's first stage) + dt sum_j a_ij k_j; NPREV stages enter (compile time).
-// FP64 mode, and the mixed mode with FP64 estimates (P.ff_est = 0): everything in
-// FP64 (the mixed mode reads FP32 k_j and rounds z to FP32 for its fluxes).  ES_FP64X
-// and the mixed float-float mode: the FP64 state is split into float-float (integer
-// pipe), the stage increment e = dt sum_j a_ij k_j, y = u + e, the parameter vector
-// and w(y) - w(u) are formed in float-float on the FP32 pipe.  FP64 selects the path
-// at compile time (the two differ widely in register use).
+// FP64 mode: everything in FP64.  Mixed mode with FP64 estimates (P.ff_est = 0):
+// e = dt sum_j a_ij k_j, y = u + e and w(y) - w(u) in FP64 (the FP32 k_j placed into
+// FP64 on the integer pipe); the parameter vector for the FP32 fluxes is formed from
+// y in float-float and rounded once.  ES_FP64X and the mixed float-float mode: the
+// FP64 state is split into float-float (integer pipe), e, y, the parameter vector and
+// w(y) - w(u) are formed in float-float on the FP32 pipe.  FP64 selects the
+// FP64-increment paths at compile time (they differ widely in register use).
 template <typename TF, int NPREV, bool FP64>
 __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __restrict__ status) {
   const long long N = (long long)P.K * sp.Np;
@@ -270,7 +300,31 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
         sp.q[v * N + g] = u[v];
       }
     }
-    if constexpr (FP64) {
+    if constexpr (FP64 && !std::is_same<TF, double>::value) {
+      double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      if constexpr (NPREV > 0) {
+        const double dt = geom_of(P, inst).dt;
+#pragma unroll
+        for (int j = 0; j < NPREV; ++j) {
+          const double c = sp.coef[j] * dt;
+          const TF* kj = static_cast<const TF*>(sp.k[j]);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) e[v] = fma(c, to_f64(kj[v * N + g]), e[v]);
+        }
+      }
+      ff yf[5], z[6];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) yf[v] = ff_from_double(u[v] + e[v]);
+      if (!param_vector_ff(yf, P.Cff, z)) atomicOr(status, kStatusNonphysical);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) aux[c * N + g] = tf_from_ff<TF>(z[c]);
+      if (sp.dw) {
+        double dw[5];
+        entropy_var_increment(u, e, gam, P.Cd.inv_gm1, dw);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sp.dw[v * N + g] = dw[v];
+      }
+    } else if constexpr (FP64) {
       double y[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) y[v] = u[v];
@@ -279,9 +333,9 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
 #pragma unroll
         for (int j = 0; j < NPREV; ++j) {
           const double c = sp.coef[j] * dt;
-          const TF* kj = static_cast<const TF*>(sp.k[j]);
+          const double* kj = static_cast<const double*>(sp.k[j]);
 #pragma unroll
-          for (int v = 0; v < 5; ++v) y[v] = fma(c, double(kj[v * N + g]), y[v]);
+          for (int v = 0; v < 5; ++v) y[v] = fma(c, kj[v * N + g], y[v]);
         }
       }
       const double rho = y[0];
@@ -292,12 +346,12 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
       // z1 = sqrt(rho/p) = rho / sqrt(rho p), z5 = sqrt(rho p)
       const double rs = rsqrt(rho * p);
       const double z1 = rho * rs;
-      aux[0 * N + g] = TF(z1);
-      aux[1 * N + g] = TF(z1 * v0);
-      aux[2 * N + g] = TF(z1 * v1);
-      aux[3 * N + g] = TF(z1 * v2);
-      aux[4 * N + g] = TF(rho * p * rs);
-      aux[5 * N + g] = TF(p * rs);  // 1/z1 = sqrt(p/rho)
+      aux[0 * N + g] = z1;
+      aux[1 * N + g] = z1 * v0;
+      aux[2 * N + g] = z1 * v1;
+      aux[3 * N + g] = z1 * v2;
+      aux[4 * N + g] = rho * p * rs;
+      aux[5 * N + g] = p * rs;  // 1/z1 = sqrt(p/rho)
       if (sp.dw) {
         double e[5], dw[5];
 #pragma unroll
@@ -332,19 +386,10 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
 #pragma unroll
         for (int v = 0; v < 5; ++v) yf[v] = uf[v];
       }
-      const ff rho = yf[0];
-      const ff ir = ff_rcp(rho);
-      const ff v0 = yf[1] * ir, v1 = yf[2] * ir, v2 = yf[3] * ir;
-      const ff p = C.gm1 * (yf[4] - ff_half(yf[1] * v0 + yf[2] * v1 + yf[3] * v2));
-      if (!(rho.hi > 0.0f) || !(p.hi > 0.0f)) atomicOr(status, kStatusNonphysical);
-      const ff rs = ff_rsqrt(rho * p);
-      const ff z1 = rho * rs;
-      const ff z[6] = {z1, z1 * v0, z1 * v1, z1 * v2, rho * p * rs, p * rs};
+      ff z[6];
+      if (!param_vector_ff(yf, C, z)) atomicOr(status, kStatusNonphysical);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        if constexpr (std::is_same<TF, ff>::value) aux[c * N + g] = z[c];
-        else aux[c * N + g] = __fadd_rn(z[c].hi, z[c].lo);
-      }
+      for (int c = 0; c < 6; ++c) aux[c * N + g] = tf_from_ff<TF>(z[c]);
       if (sp.dw) {
         ff dw[5];
         entropy_var_increment_ff(uf, ef, C, dw);
@@ -714,14 +759,14 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
       const double Pn = mass_weight<P1>(P, G.J, n);
       double k[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) k[v] = double(acc[v * EPB * Np + t]);
+      for (int v = 0; v < 5; ++v) k[v] = to_f64(acc[v * EPB * Np + t]);
       if (sv.d_out) {
         const double dt = G.dt;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           double dv = (sv.dcoef_self * dt) * k[v];
           for (int j = 0; j < sv.nd; ++j)
-            dv = fma(sv.dcoef[j] * dt, double(static_cast<const TF*>(sv.dk[j])[v * N + g]), dv);
+            dv = fma(sv.dcoef[j] * dt, to_f64(static_cast<const TF*>(sv.dk[j])[v * N + g]), dv);
           sv.d_out[v * N + g] = dv;
         }
       } else if (sv.kout64) {
@@ -740,7 +785,7 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
         z_to_w(s, C, w);
         double sum = 0.0;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) sum += double(w[v]) * k[v];
+        for (int v = 0; v < 5; ++v) sum += to_f64(w[v]) * k[v];
         red[t] = Pn * sum;
       }
       if (wantA) {
