@@ -81,6 +81,11 @@ typedef struct {
                            <= 0 selects 1e-8 (ES_FP64, ES_FP64X) or 4e-6 (ES_MIXED,
                            ES_MIXED_FF:
                            64 eps_32, above the FP32 right-hand side's rounding noise) */
+  double visc_diss;     /* diss^V coefficient alpha >= 0 (used when mu > 0; 0 = off):
+                           interior penalty on the entropy-variable jump at every face,
+                           alpha (2/h_m)(1/omega_0) (C_mm(q-) + C_mm(q+))/2 (w- - w+)
+                           added to the interface flux, C_mm the viscous-flux block
+                           of dw/dx_m (symmetric positive semidefinite) */
 } es_config;
 
 /* Mesh, LGL/SBP tables (Section 3.1: diagonal-norm SBP on LGL nodes) and

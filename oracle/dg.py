@@ -15,7 +15,13 @@ dissipation and viscous details to its references; the readings taken here:
   entropy-conservative flux minus diss * Rusanov dissipation.
 * Viscous terms: BR1 in entropy variables.  theta_m = (2/h_m)[D w + lifting
   toward the face average of w], viscous flux F^V_m(q, theta), divergence
-  (2/h_m)[D F^V_m + lifting toward the face average of F^V_m].  diss^V = 0.
+  (2/h_m)[D F^V_m + lifting toward the face average of F^V_m].
+* diss^V (its construction is deferred to the references; off unless
+  Physics.visc_diss = alpha > 0): an interior penalty on the jump of the entropy
+  variables, g = sigma_m Chat (w - w+) added to the interface flux like diss^I,
+  Chat = (C_mm(q) + C_mm(q+))/2, sigma_m = alpha (2/h_m)/omega_0.  Chat is symmetric
+  positive semidefinite, so each face removes sigma [[w]]^T Chat [[w]] >= 0 of entropy
+  and the two sides' terms cancel in the conservation sums.
 * Mesh: n_x x n_y x n_z elements of size h_x x h_y x h_z, periodic in every
   direction unless a Dirichlet-penalty boundary is given for it; metric 2/h_m per
   direction, Jacobian h_x h_y h_z / 8.
@@ -39,12 +45,13 @@ _AXES = {0: (3, 6), 1: (2, 5), 2: (1, 4)}
 
 
 class Physics:
-    def __init__(self, gamma=1.4, mu=0.0, Pr=0.72, R=1.0, diss=0):
+    def __init__(self, gamma=1.4, mu=0.0, Pr=0.72, R=1.0, diss=0, visc_diss=0.0):
         self.gamma = float(gamma)
         self.mu = float(mu)
         self.Pr = float(Pr)
         self.R = float(R)
         self.diss = diss
+        self.visc_diss = float(visc_diss)
 
 
 class Mesh:
@@ -240,12 +247,53 @@ def viscous_term(mesh, U, phys, return_parts=False, t=0.0):
     return out
 
 
+def _penalty_fluxes(mesh, U, phys, m, t):
+    """diss^V penalty fluxes sigma_m Chat (w_minus - w_plus) on the +x_m and -x_m faces of
+    every element, oriented along +x_m (exterior states on boundary faces)."""
+    g = phys.gamma
+    p = mesh.p
+    eax, nax = _AXES[m]
+    sig = phys.visc_diss * (2.0 / mesh.h[m]) / mesh.omega[p]
+
+    def flux(qa, qb):
+        C = 0.5 * (gas.viscous_jacobian(qa, g, phys.mu, phys.Pr, phys.R, m)
+                   + gas.viscous_jacobian(qb, g, phys.mu, phys.Pr, phys.R, m))
+        jump = gas.entropy_variables(qa, g) - gas.entropy_variables(qb, g)
+        return sig * np.einsum("ij...,j...->i...", C, jump)
+    q_right = _face(U, p, nax)
+    q_left = _face(U, 0, nax)
+    g_right = flux(q_right, _next_trace(mesh, q_left, m, eax, t))
+    g_left = np.roll(g_right, 1, axis=eax)
+    if m in mesh.bc:
+        gb = flux(_prev_trace(mesh, q_right, m, eax, t), q_left)
+        idx = [slice(None)] * g_left.ndim
+        idx[eax] = 0
+        g_left[tuple(idx)] = gb[tuple(idx)]
+    return g_right, g_left
+
+
+def viscous_interface_dissipation(mesh, U, phys, t=0.0):
+    """diss^V at the faces of every element: -(2/h_m)(1/omega) g on the +x_m face,
+    +(2/h_m)(1/omega) g on the -x_m face, with g the penalty flux through that face."""
+    p = mesh.p
+    out = np.zeros_like(U)
+    for m in range(3):
+        _, nax = _AXES[m]
+        s = 2.0 / mesh.h[m]
+        g_right, g_left = _penalty_fluxes(mesh, U, phys, m, t)
+        _add_face(out, p, nax, -s / mesh.omega[p] * g_right)
+        _add_face(out, 0, nax, s / mesh.omega[0] * g_left)
+    return out
+
+
 def rhs(mesh, U, phys, t=0.0):
     """f(u) of Eq. (ode): the right-hand side dq/dt of Eq. (compressible_ns_diss) at time
     t (t only enters through prescribed boundary states)."""
     out = volume_term(mesh, U, phys) + inviscid_surface_term(mesh, U, phys, t)
     if phys.mu != 0.0:
         out = out + viscous_term(mesh, U, phys, t=t)
+        if phys.visc_diss > 0.0:
+            out = out + viscous_interface_dissipation(mesh, U, phys, t)
     return out
 
 
@@ -274,6 +322,11 @@ def rhs_term_magnitude(mesh, U, phys, t=0.0):
         for m in range(3):
             eax, nax = _AXES[m]
             T += (2.0 / mesh.h[m]) * _apply_D(np.abs(mesh.D), np.abs(fv[m]), nax)
+            if phys.visc_diss > 0.0:
+                s = 2.0 / mesh.h[m]
+                g_right, g_left = _penalty_fluxes(mesh, U, phys, m, t)
+                _add_face(T, p, nax, s / mesh.omega[p] * np.abs(g_right))
+                _add_face(T, 0, nax, s / mesh.omega[0] * np.abs(g_left))
     return T
 
 

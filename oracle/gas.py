@@ -208,3 +208,26 @@ def viscous_flux(q, theta, g, mu, Pr, R):
             fv[m, 4] = fv[m, 4] + tau_mk * v[k]
         fv[m, 4] = fv[m, 4] + kappa * grad_T[m]
     return fv
+
+
+def viscous_jacobian(q, g, mu, Pr, R, m):
+    """C_mm(q), the block of F^V_m = sum_j C_mj dw/dx_j that multiplies dw/dx_m, written
+    out as a 5 x 5 matrix per node (shape (5, 5, ...)); Section 3.1 cites the C_mj.
+
+    With RT = p/rho, the velocity part of a w-gradient g is b = M g, M = [0 | I_3 | v]
+    (d v = RT (d w_{2..4} + v d w_5)), and d T = R T^2 d w_5, so
+        C_mm = mu RT M^T (I + e_m e_m^T / 3) M + kappa R T^2 e_5 e_5^T,
+    symmetric positive semidefinite.
+    """
+    rho, v, p = primitives(q, g)
+    RT = p / rho
+    kappa = mu * g * R / ((g - 1.0) * Pr)
+    M = np.zeros((3, 5) + rho.shape)
+    for k in range(3):
+        M[k, 1 + k] = 1.0
+        M[k, 4] = v[k]
+    N = np.eye(3)
+    N[m, m] += 1.0 / 3.0
+    C = mu * RT * np.einsum("ki...,kl,lj...->ij...", M, N, M)
+    C[4, 4] = C[4, 4] + kappa * RT * RT / R
+    return C

@@ -38,7 +38,8 @@ class es_config(ctypes.Structure):
                 ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
                 ("gamma_gas", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("R", ctypes.c_double), ("interface_diss", ctypes.c_int), ("relax", ctypes.c_int),
-                ("rk", ctypes.c_int), ("precision", ctypes.c_int), ("delta_floor", ctypes.c_double)]
+                ("rk", ctypes.c_int), ("precision", ctypes.c_int), ("delta_floor", ctypes.c_double),
+                ("visc_diss", ctypes.c_double)]
 
 
 class ESError(RuntimeError):
@@ -165,7 +166,8 @@ def _stream(stream):
 
 
 def make_config(p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0,
-                interface_diss=1, relax=ES_RELAX_LOCAL, rk=ES_RK_BS3, precision=ES_FP64, delta_floor=0.0):
+                interface_diss=1, relax=ES_RELAX_LOCAL, rk=ES_RK_BS3, precision=ES_FP64, delta_floor=0.0,
+                visc_diss=0.0):
     c = es_config()
     c.p = p
     c.nx, c.ny, c.nz = n
@@ -174,6 +176,7 @@ def make_config(p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma_gas=1.4, mu=
     c.gamma_gas, c.mu, c.Pr, c.R = gamma_gas, mu, Pr, R
     c.interface_diss, c.relax, c.rk, c.precision = interface_diss, relax, rk, precision
     c.delta_floor = delta_floor
+    c.visc_diss = visc_diss
     return c
 
 

@@ -123,6 +123,7 @@ int validate_config(const es_config& C) {
   if (!(C.gamma_gas > 1.0) || !(C.R > 0.0) || C.mu < 0.0 || (C.mu > 0.0 && !(C.Pr > 0.0))) return ES_ERR_INVALID;
   if (C.rk != ES_RK_BS3 && C.rk != ES_RK_RK4) return ES_ERR_INVALID;
   if (C.precision < ES_FP64 || C.precision > ES_MIXED_FF) return ES_ERR_INVALID;
+  if (!(C.visc_diss >= 0.0) || !std::isfinite(C.visc_diss)) return ES_ERR_INVALID;
   if (C.relax != ES_RELAX_NONE && C.relax != ES_RELAX_LOCAL && C.relax != ES_RELAX_GLOBAL) return ES_ERR_INVALID;
   if (C.interface_diss < 0 || C.interface_diss > 2) return ES_ERR_INVALID;
   for (int m = 0; m < 3; ++m)
@@ -187,6 +188,7 @@ void build_params(const es_config& C, Params* out) {
   P.p1 = P1;
   P.ninst = 1;
   P.ff_est = (C.precision == ES_MIXED_FF || C.precision == ES_FP64X) ? 1 : 0;
+  P.visc_pen = C.mu > 0.0 ? C.visc_diss : 0.0;
   P.g0 = instance_geom(C, 0);
   P.geom = nullptr;
   P.elem_inst = nullptr;
@@ -1005,7 +1007,7 @@ namespace {
 bool same_physics(const es_config& a, const es_config& b) {
   return a.gamma_gas == b.gamma_gas && a.mu == b.mu && (a.mu == 0.0 || a.Pr == b.Pr) && a.R == b.R &&
          a.interface_diss == b.interface_diss && a.relax == b.relax && a.rk == b.rk && a.precision == b.precision &&
-         a.delta_floor == b.delta_floor;
+         a.delta_floor == b.delta_floor && a.visc_diss == b.visc_diss;
 }
 
 void batch_free(es_batch* b) {

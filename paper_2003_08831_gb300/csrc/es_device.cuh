@@ -61,6 +61,7 @@ struct Params {
   double gam;                  // ratio of specific heats
   double mu, kappa_heat, R;    // viscosity, heat conductivity mu c_p / Pr, gas constant
   double inv_R;                // 1/R
+  double visc_pen;             // diss^V coefficient alpha (0: off; only with mu > 0)
   FluxConst<double> Cd;        // flux constants per precision (host-computed: no
   FluxConst<float> Cf;         // divisions or square roots in the kernels)
   FluxConst<ff> Cff;

@@ -496,6 +496,46 @@ __device__ __forceinline__ void face_flux(const Zstate<TF>& L, TF izL, const Zst
   }
 }
 
+// diss^V (interior penalty on the entropy-variable jump): C_mm(s) g for one side's
+// state, accumulated into c.  C_mm is the block of the viscous flux F^V_m that
+// multiplies dw/dx_m; with RT = p/rho = 1/z1^2, v = z_{2..4}/z1 and the velocity part
+// b = g_{2..4} + v g_5 of the jump g (w_1 does not enter):
+// C_mm g = (0, mu RT (b + e_m b_m/3), v . [mu RT (b + e_m b_m/3)] + kappa (RT)^2/R g_5).
+template <typename TF>
+__device__ __forceinline__ void visc_jump_flux(const Zstate<TF>& s, TF iz, const TF g[4], int m, TF mu, TF kap,
+                                               TF iR, TF c[5]) {
+  const TF v0 = s.z[1] * iz, v1 = s.z[2] * iz, v2 = s.z[3] * iz;
+  const TF RT = iz * iz;
+  const TF mrt = mu * RT;
+  TF t0 = mrt * (g[0] + v0 * g[3]);
+  TF t1 = mrt * (g[1] + v1 * g[3]);
+  TF t2 = mrt * (g[2] + v2 * g[3]);
+  if (m == 0) t0 += TF(1.0 / 3.0) * t0;
+  else if (m == 1) t1 += TF(1.0 / 3.0) * t1;
+  else t2 += TF(1.0 / 3.0) * t2;
+  c[1] += t0;
+  c[2] += t1;
+  c[3] += t2;
+  c[4] += t0 * v0 + t1 * v1 + t2 * v2 + kap * RT * RT * iR * g[3];
+}
+
+// adds sig (C_mm(L) + C_mm(R))/2 (w_L - w_R) to the interface flux f (w_{2..5} = z1 z_{2..4}, -z1^2)
+template <typename TF>
+__device__ __forceinline__ void visc_penalty(const Zstate<TF>& L, TF izL, const Zstate<TF>& R, TF izR, int m,
+                                             TF sig, const Params& P, TF f[5]) {
+  TF g[4];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g[k] = L.z[0] * L.z[1 + k] - R.z[0] * R.z[1 + k];
+  g[3] = R.z[0] * R.z[0] - L.z[0] * L.z[0];
+  const TF mu = TF(P.mu), kap = TF(P.kappa_heat), iR = TF(P.inv_R);
+  TF c[5] = {TF(0), TF(0), TF(0), TF(0), TF(0)};
+  visc_jump_flux(L, izL, g, m, mu, kap, iR, c);
+  visc_jump_flux(R, izR, g, m, mu, kap, iR, c);
+  const TF hs = TF(0.5) * sig;
+#pragma unroll
+  for (int v = 1; v < 5; ++v) f[v] += hs * c[v];
+}
+
 // a prescribed boundary state's parameter vector and 1/z1 in the flux precision
 template <typename TF>
 __device__ __forceinline__ Zstate<TF> bc_z(const double* v, TF& iz) {
@@ -506,7 +546,9 @@ __device__ __forceinline__ Zstate<TF> bc_z(const double* v, TF& iz) {
   return z;
 }
 
-template <int P1, typename TF>
+// VPEN: with the diss^V penalty (a separate instantiation keeps the common path's
+// register count)
+template <int P1, typename TF, bool VPEN>
 __global__ void k_face(Params P, const TF* __restrict__ aux, TF* __restrict__ F, TF* __restrict__ FL) {
   constexpr int P2 = P1 * P1, Np = P1 * P2;
   const long long N = (long long)P.K * Np;
@@ -532,13 +574,22 @@ __global__ void k_face(Params P, const TF* __restrict__ aux, TF* __restrict__ F,
     }
     TF f[5];
     face_flux(L, izL, R, izR, m, C, P.diss, f);
+    // diss^V penalty scale alpha (2/h_m)(1/omega_0)
+    TF sig = TF(0);
+    if constexpr (VPEN) {
+      sig = TF(P.visc_pen * geom_of(P, inst_of(P, e)).metric[m] * P.inv_omega_end);
+      visc_penalty(L, izL, R, izR, m, sig, P, f);
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[((long long)(m * 5 + v) * P.K + e) * P2 + ab] = f[v];
     if (at_boundary(P, e, m, 0)) {  // -x_m boundary face of this element, into FL
       TF izB;
       const Zstate<TF> B = bc_z<TF>(bc_values(P, m, 0), izB);
       const long long g0 = (long long)e * Np + line_node<P1>(m, a, b, 0);
-      face_flux(B, izB, load_z<P1, TF>(aux, N, g0), aux[5 * N + g0], m, C, P.diss, f);
+      const Zstate<TF> I = load_z<P1, TF>(aux, N, g0);
+      const TF izI = aux[5 * N + g0];
+      face_flux(B, izB, I, izI, m, C, P.diss, f);
+      if constexpr (VPEN) visc_penalty(B, izB, I, izI, m, sig, P, f);
 #pragma unroll
       for (int v = 0; v < 5; ++v) FL[((long long)(m * 5 + v) * P.K + e) * P2 + ab] = f[v];
     }
@@ -1390,7 +1441,10 @@ void Launcher<P1, TF>::prep(const Params& P, const StagePrep& sp, void* aux, int
 
 template <int P1, typename TF>
 void Launcher<P1, TF>::face(const Params& P, const void* aux, void* F, void* FL, cudaStream_t st, int grid) {
-  k_face<P1, TF><<<grid, 256, 0, st>>>(P, static_cast<const TF*>(aux), static_cast<TF*>(F), static_cast<TF*>(FL));
+  if (P.visc_pen > 0.0)
+    k_face<P1, TF, true><<<grid, 256, 0, st>>>(P, static_cast<const TF*>(aux), static_cast<TF*>(F), static_cast<TF*>(FL));
+  else
+    k_face<P1, TF, false><<<grid, 256, 0, st>>>(P, static_cast<const TF*>(aux), static_cast<TF*>(F), static_cast<TF*>(FL));
 }
 
 template <int P1, typename TF>

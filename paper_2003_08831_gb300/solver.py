@@ -43,7 +43,7 @@ def load_checkpoint(path):
 class Solver:
     def __init__(self, p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0,
                  interface_diss=1, relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64,
-                 delta_floor=0.0, device="cuda"):
+                 delta_floor=0.0, device="cuda", visc_diss=0.0):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -55,7 +55,7 @@ class Solver:
         self.K = self.n[0] * self.n[1] * self.n[2]
         self.N = self.K * self.Np
         self.cfg = B.make_config(p, n, lo, hi, gamma_gas, mu, Pr, R, interface_diss, relax, rk, precision,
-                                 delta_floor)
+                                 delta_floor, visc_diss)
         with torch.cuda.device(self.device):
             self.ctx = B.es_create(self.cfg)
 
@@ -124,7 +124,7 @@ class Solver:
         c = self.cfg
         return {"p": c.p, "n": [c.nx, c.ny, c.nz], "lo": list(c.lo), "hi": list(c.hi), "gamma_gas": c.gamma_gas,
                 "mu": c.mu, "Pr": c.Pr, "R": c.R, "interface_diss": c.interface_diss, "relax": c.relax,
-                "rk": c.rk, "precision": c.precision, "delta_floor": c.delta_floor}
+                "rk": c.rk, "precision": c.precision, "delta_floor": c.delta_floor, "visc_diss": c.visc_diss}
 
     def checkpoint(self, path, q, t, step, dt):
         """Write the device state q, time t (float) and step counter to path (see save_checkpoint)."""
@@ -137,7 +137,8 @@ class Solver:
         q, h = load_checkpoint(path)
         c = h["config"]
         s = cls(c["p"], tuple(c["n"]), tuple(c["lo"]), tuple(c["hi"]), c["gamma_gas"], c["mu"], c["Pr"], c["R"],
-                c["interface_diss"], c["relax"], c["rk"], c["precision"], c["delta_floor"], device=device)
+                c["interface_diss"], c["relax"], c["rk"], c["precision"], c["delta_floor"], device=device,
+                visc_diss=c.get("visc_diss", 0.0))
         return s, s.to_device(q), h["t"], h["step"], h["dt"]
 
     def set_boundary(self, direction, kind, params=None):
@@ -180,10 +181,11 @@ class BatchSolver:
     """Many independent instances (possibly different degrees and element counts)."""
 
     def __init__(self, instances, gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0, interface_diss=1,
-                 relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64, delta_floor=0.0):
+                 relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64, delta_floor=0.0, visc_diss=0.0):
         """instances: list of dicts with p, n (nx, ny, nz), lo, hi."""
         self.cfgs = [B.make_config(d["p"], d["n"], d.get("lo", (0.0, 0.0, 0.0)), d.get("hi", (1.0, 1.0, 1.0)),
-                                   gamma_gas, mu, Pr, R, interface_diss, relax, rk, precision, delta_floor)
+                                   gamma_gas, mu, Pr, R, interface_diss, relax, rk, precision, delta_floor,
+                                   visc_diss)
                      for d in instances]
         self.instances = instances
         self.count = len(instances)

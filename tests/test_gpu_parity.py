@@ -154,7 +154,8 @@ def compare_advance(mesh, U, lo, hi, phys, tabname, nsteps, mode="local", cfl=0.
     sens_g, sens_gk = gamma_sensitivity(mesh, U, dt, nsteps, phys, rk.TABLEAUX[tabname], mode, hist, eps=eps)
     relax_mode = {"local": B.ES_RELAX_LOCAL, "global": B.ES_RELAX_GLOBAL, "none": B.ES_RELAX_NONE}[mode]
     s = solver(mesh.p, mesh.n, lo, hi, mu=phys.mu, Pr=phys.Pr, interface_diss=phys.diss,
-               rk=B.ES_RK_BS3 if tabname == "BS3" else B.ES_RK_RK4, relax=relax_mode, **kw)
+               rk=B.ES_RK_BS3 if tabname == "BS3" else B.ES_RK_RK4, relax=relax_mode,
+               visc_diss=phys.visc_diss, **kw)
     q = s.to_device(U)
     t, gh, gk = s.advance(q, nsteps, dt)
     assert s.status() == 0
@@ -495,3 +496,33 @@ def test_rhs_matrix_dissipation(p, n, mu, prec):
 def test_advance_matrix_dissipation():
     mesh, U, lo, hi = vortex_setup(N=4, p=3, nz=2)
     compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=2), "BS3", 10)
+
+
+# ---------------------------------------------------------------------------------------
+# diss^V: interior penalty on the entropy-variable jump (visc_diss = alpha)
+
+@pytest.mark.parametrize("p,n,mu,alpha,diss,prec", [(2, (3, 5, 4), 0.02, 1.0, 1, 0), (3, (4, 3, 5), 0.01, 0.5, 2, 0),
+                                                    (4, (2, 3, 3), 0.05, 1.0, 1, 0), (5, (2, 2, 3), 0.02, 2.0, 0, 0),
+                                                    (3, (4, 3, 5), 0.01, 1.0, 1, 2)])
+def test_rhs_viscous_interface_dissipation(p, n, mu, alpha, diss, prec):
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.5, 2.0)
+    mesh = dg.Mesh(p, n, lo, hi)
+    U = random_state(mesh, seed=p * 11 + n[1])
+    phys = dg.Physics(G, mu=mu, Pr=0.72, diss=diss, visc_diss=alpha)
+    ref = dg.rhs(mesh, U, phys)
+    s = solver(p, n, lo, hi, mu=mu, interface_diss=diss, precision=prec, visc_diss=alpha)
+    dq = s.rhs(s.to_device(U)).cpu().numpy()
+    assert s.status() == 0
+    s.close()
+    assert_rhs_close(dq, ref, dg.rhs_term_magnitude(mesh, U, phys), eps=EPS if prec == 0 else 2.0 ** -47)
+    # the penalty is really there: without it the right-hand side differs by far more than the bar
+    ref0 = dg.rhs(mesh, U, dg.Physics(G, mu=mu, Pr=0.72, diss=diss))
+    assert np.max(rel_err_per_var(ref0, ref)) > 1e-6
+
+
+def test_advance_viscous_interface_dissipation():
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    mesh = dg.Mesh(3, (3, 3, 3), lo, hi)
+    U = random_state(mesh, seed=77, noise=0.01)
+    compare_advance(mesh, U, lo, hi, dg.Physics(G, mu=0.01, Pr=0.72, diss=1, visc_diss=1.0), "BS3", 5)
+

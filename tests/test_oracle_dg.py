@@ -175,3 +175,28 @@ def test_viscous_term_consistency():
         assert np.max(np.abs(V[0])) < 1e-14
     assert errs[1] < errs[0] / 4, errs
     assert errs[1] < 1e-3 * mu * k * k * A
+
+
+@pytest.mark.parametrize("p,n", MESHES)
+def test_viscous_interface_dissipation(p, n):
+    """diss^V: zero on a uniform state and (to rounding) on data continuous across the
+    faces, conservative, and strictly entropy-dissipative on data that jumps."""
+    mesh = dg.Mesh(p, n, (0, 0, 0), (1.0, 2.0, 1.5))
+    phys = dg.Physics(G, mu=0.02, Pr=0.72, diss=1, visc_diss=1.0)
+    U = np.empty(mesh.shape)
+    U[:] = gas.conserved(np.array(1.3), np.array([0.4, -0.7, 0.2]), np.array(0.8), G).reshape(5, 1, 1, 1, 1, 1, 1)
+    assert np.max(np.abs(dg.viscous_interface_dissipation(mesh, U, phys))) == 0.0
+    Us = smooth_state(mesh, seed=40 + p)
+    ref = np.max(np.abs(dg.viscous_term(mesh, Us, phys)))
+    assert np.max(np.abs(dg.viscous_interface_dissipation(mesh, Us, phys))) < 1e-11 * ref
+    U = smooth_state(mesh, seed=50 + p, noise=0.05)
+    V = dg.viscous_interface_dissipation(mesh, U, phys)
+    scale = np.sum(mesh.element_sum(np.abs(V)))
+    assert max(abs(np.sum(mesh.element_sum(V[v]))) for v in range(5)) < 1e-13 * scale
+    W = gas.entropy_variables(U, G)
+    dS = np.sum(mesh.element_sum(np.sum(W * V, axis=0)))
+    assert dS < -1e-3 * np.sum(mesh.element_sum(np.sum(np.abs(W * V), axis=0)))
+    # and it enters rhs() only with a viscosity and a positive coefficient
+    R1 = dg.rhs(mesh, U, phys)
+    R0 = dg.rhs(mesh, U, dg.Physics(G, mu=0.02, Pr=0.72, diss=1))
+    assert np.max(np.abs(R1 - R0 - V)) < 1e-12 * np.max(np.abs(R0))

@@ -247,3 +247,42 @@ def test_hessian_form_against_second_derivative():
         f = lambda t, n=n: mp_S_at(u[:, n], d[:, n], t)
         ref = mp.diff(f, 0, 2)
         assert abs(H[n] - float(ref)) <= 1e-12 * abs(float(ref))
+
+
+@pytest.mark.parametrize("m", [0, 1, 2])
+def test_viscous_jacobian_against_definition(m):
+    """C_mm g against the viscous flux of its definition: the velocity and temperature
+    derivatives along x_m that the w-gradient g implies (v = -w_{2..4}/w_5 and
+    T = -1/(R w_5), differentiated in 40 digits), Stokes' stress and Fourier's law.
+    C_mm is symmetric positive semidefinite and has no first row or column."""
+    mu, Pr, R = 0.03, 0.72, 1.3
+    qs = rand_states(6, 20 + m)
+    rng = np.random.default_rng(30 + m)
+    gs = rng.normal(size=(5, 6))
+    C = gas.viscous_jacobian(qs, G, mu, Pr, R, m)
+    assert C.shape == (5, 5, 6)
+    scale = np.max(np.abs(C))
+    assert np.max(np.abs(C - np.swapaxes(C, 0, 1))) <= 1e-15 * scale
+    assert np.max(np.abs(C[0])) == 0.0 and np.max(np.abs(C[:, 0])) == 0.0
+    kappa = mu * G * R / ((G - 1) * Pr)
+    for i in range(6):
+        assert np.min(np.linalg.eigvalsh(C[:, :, i])) >= -1e-14 * scale
+        rho, m1, m2, m3, E = [mp.mpf(float(a)) for a in qs[:, i]]
+        p = (mp.mpf(G) - 1) * (E - (m1 * m1 + m2 * m2 + m3 * m3) / (2 * rho))
+        w = [m1 / p, m2 / p, m3 / p, -rho / p]              # rho v/p and -rho/p
+        g = [mp.mpf(float(a)) for a in gs[1:, i]]
+
+        def vel(eps, k):
+            return -(w[k] + eps * g[k]) / (w[3] + eps * g[3])
+
+        def temp(eps):
+            return -1 / (mp.mpf(R) * (w[3] + eps * g[3]))
+        dv = [mp.diff(lambda e, k=k: vel(e, k), 0) for k in range(3)]
+        dT = mp.diff(temp, 0)
+        v = [m1 / rho, m2 / rho, m3 / rho]
+        tau = [mu * (dv[k] + (dv[m] if k == m else 0) - (mp.mpf(2) / 3 * dv[m] if k == m else 0))
+               for k in range(3)]
+        f = [0, tau[0], tau[1], tau[2], sum(tau[k] * v[k] for k in range(3)) + kappa * dT]
+        got = C[:, :, i] @ gs[:, i]
+        ref = np.array([float(a) for a in f])
+        assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref)), (i, got, ref)
