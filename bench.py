@@ -105,7 +105,7 @@ def kernel_flops(p, n_el, stages=3):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_volume launch of the
 # default workload, from the ncu capture summarised in profiles/ (stage 3 of a step, FP64).
 # It is reported only while the kernel sources hash to the value the capture was taken with.
-VOLUME_TRAFFIC = {"source_sha1": "4f992d46fb0cb8165a914d78ae54ee2cc0eb2db4", "bytes_per_launch": 399566592 + 68267520}
+VOLUME_TRAFFIC = {"source_sha1": "424b9f041b2902d328ea9812e7cbd6081afe0884", "bytes_per_launch": 399509760 + 67806208}
 
 
 def kernel_source_sha1():
