@@ -43,6 +43,9 @@ extern "C" {
 
 #define ES_RK_BS3 0 /* Bogacki--Shampine 3(2), b = (2/9, 1/3, 4/9, 0) */
 #define ES_RK_RK4 1 /* classical RK(4,4) */
+#define ES_RK_RK65 2 /* Butcher's six-stage fifth-order method, b = (7, 0, 32, 12, 32, 7)/90
+                       (Section 4 pairs p = 4 with a fifth-order BSRK(8,5) whose coefficients
+                       it does not print; es_set_tableau loads any explicit tableau) */
 
 #define ES_FP64 0  /* every operation in FP64 */
 #define ES_MIXED 1 /* FP32 fluxes/SATs/viscous terms; FP64 state, stage states,
@@ -137,6 +140,16 @@ int es_set_boundary(es_ctx* ctx, int dir, int kind, const double* params, int np
 /* Sets the time at which es_rhs evaluates prescribed boundary states (host value;
  * synchronous).  ES_ERR_INVALID for a non-finite t. */
 int es_set_time(es_ctx* ctx, double t);
+
+/* Replaces the context's Runge--Kutta method (Eq. (RK-step)) by the explicit tableau
+ * with s <= 10 stages: a (host, s x s row-major, a[i*s + j] = a_ij, zero on and above
+ * the diagonal), weights b[s] and stage times c[s] (host; copied, the caller keeps
+ * ownership).  Requirements, else ES_ERR_INVALID: finite entries, a strictly lower
+ * triangular, sum_j a_ij = c_i and sum_i b_i = 1 (1e-13), and b_i >= 0 unless the
+ * context relaxes nothing (the entropy estimate Eq. (eta-est-1-RK) needs b_i >= 0).
+ * Trailing stages with b_i = 0 are not evaluated.  Stage buffers are allocated here
+ * (ES_ERR_NOMEM).  Takes effect with the next es_advance; no check of the order. */
+int es_set_tableau(es_ctx* ctx, int s, const double* a, const double* b, const double* c);
 
 /* One relaxation (last row of Eq. (relaxation-local-gamma), Theorem 2.3):
  * for every element the root gamma_elem[e] > 0 of

@@ -11,6 +11,9 @@ Tableaux (Section 4 names them; the paper prints no coefficients):
           a21 = 1/2, a32 = 3/4, a4 = (2/9, 1/3, 4/9), b = (2/9, 1/3, 4/9, 0).
           b_4 = 0, so only three stages enter u_new and the estimate.
 * RK4  -- the classical four-stage method, b = (1/6, 1/3, 1/3, 1/6).
+* RK65 -- Butcher's (1964) six-stage fifth-order method, c = (0, 1/4, 1/4, 1/2, 3/4, 1),
+          b = (7, 0, 32, 12, 32, 7)/90 >= 0: a fifth-order method for p = 4 in place of
+          the BSRK(8,5) that Section 4 names without printing it.
 
 Relaxation modes: 'local' (this paper), 'global' (one gamma for the sum of the
 local entropies, Eqs. (u-n-gamma), (t-n-gamma)), 'none' (gamma = 1, the baseline).
@@ -41,7 +44,20 @@ RK4 = {
     "order": 4,
 }
 
-TABLEAUX = {"BS3": BS3, "RK4": RK4}
+RK65 = {
+    "name": "RK65",
+    "A": np.array([[0.0, 0.0, 0.0, 0.0, 0.0, 0.0],
+                   [1.0 / 4.0, 0.0, 0.0, 0.0, 0.0, 0.0],
+                   [1.0 / 8.0, 1.0 / 8.0, 0.0, 0.0, 0.0, 0.0],
+                   [0.0, -1.0 / 2.0, 1.0, 0.0, 0.0, 0.0],
+                   [3.0 / 16.0, 0.0, 0.0, 9.0 / 16.0, 0.0, 0.0],
+                   [-3.0 / 7.0, 2.0 / 7.0, 12.0 / 7.0, -12.0 / 7.0, 8.0 / 7.0, 0.0]]),
+    "b": np.array([7.0, 0.0, 32.0, 12.0, 32.0, 7.0]) / 90.0,
+    "c": np.array([0.0, 1.0 / 4.0, 1.0 / 4.0, 1.0 / 2.0, 3.0 / 4.0, 1.0]),
+    "order": 5,
+}
+
+TABLEAUX = {"BS3": BS3, "RK4": RK4, "RK65": RK65}
 
 
 def used_stages(tab):

@@ -18,7 +18,7 @@ ES_ERR_NONPHYSICAL = -3
 ES_ERR_NO_ROOT = -4
 ES_ERR_NOMEM = -6
 ES_ERR_TOO_LARGE = -7
-ES_RK_BS3, ES_RK_RK4 = 0, 1
+ES_RK_BS3, ES_RK_RK4, ES_RK_RK65 = 0, 1, 2
 ES_FP64, ES_MIXED, ES_FP64X, ES_MIXED_FF = 0, 1, 2, 3
 ES_RELAX_NONE, ES_RELAX_LOCAL, ES_RELAX_GLOBAL = 0, 1, 2
 ES_BC_PERIODIC, ES_BC_STATE, ES_BC_VISCOUS_SHOCK = 0, 1, 2
@@ -29,7 +29,7 @@ EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "
            "es_autotune", "es_batch_create", "es_batch_destroy", "es_batch_nodes", "es_batch_node_coords",
            "es_batch_set_state", "es_batch_get_state", "es_batch_set_dt", "es_batch_autotune",
            "es_batch_volume_variant", "es_batch_advance", "es_batch_times", "es_batch_status",
-           "es_batch_launch_count", "es_reciprocal", "es_set_boundary", "es_set_time"]
+           "es_batch_launch_count", "es_reciprocal", "es_set_boundary", "es_set_time", "es_set_tableau"]
 KERNEL_KINDS = ["prep", "face", "grad", "volume", "relax", "other"]
 
 
@@ -123,6 +123,8 @@ def load(path=None):
     lib.es_set_boundary.restype = i
     lib.es_set_time.argtypes = [vp, d]
     lib.es_set_time.restype = i
+    lib.es_set_tableau.argtypes = [vp, i, vp, vp, vp]
+    lib.es_set_tableau.restype = i
     lib.es_strerror.argtypes = [i]
     lib.es_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -210,6 +212,18 @@ def es_set_boundary(ctx, direction, kind, params=None):
 
 def es_set_time(ctx, t):
     _check(load().es_set_time(ctx, float(t)), "es_set_time")
+
+
+def es_set_tableau(ctx, A, b, c):
+    """A (s x s, strictly lower triangular), b, c: host sequences of floats."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    s = b.size
+    if A.shape != (s, s) or c.size != s:
+        raise ValueError("tableau shapes: A (s, s), b (s,), c (s,)")
+    _check(load().es_set_tableau(ctx, s, A.ctypes.data, b.ctypes.data, c.ctypes.data), "es_set_tableau")
 
 
 def es_relax_step(ctx, u_old, u_new, d_eta, gamma_elem, gamma, u_out, stream=None):

@@ -76,12 +76,13 @@ void lgl_tables(int p, double* x, double* w, double* D) {
   D[p * n + p] = p * (p + 1) / 4.0;
 }
 
-// Butcher tableaux (Section 4 names BSRK(4,3) and RK(4,4)).
+// Butcher tableaux (Section 4 names BSRK(4,3), RK(4,4) and, for p = 4, 5, BSRK(8,5)
+// and VRK(9,6), whose coefficients it does not print).
 struct Tableau {
-  int s;          // stages entering u_new
-  double a[4][4];
-  double b[4];
-  double c[4];    // stage times (boundary states are evaluated at t + c_i dt)
+  int s;          // stages entering u_new (trailing stages with b_i = 0 dropped)
+  double a[kMaxStages][kMaxStages];
+  double b[kMaxStages];
+  double c[kMaxStages];  // stage times (boundary states are evaluated at t + c_i dt)
 };
 
 Tableau tableau(int rk) {
@@ -96,6 +97,30 @@ Tableau tableau(int rk) {
     t.b[0] = 2.0 / 9.0;
     t.b[1] = 1.0 / 3.0;
     t.b[2] = 4.0 / 9.0;
+  } else if (rk == ES_RK_RK65) {  // Butcher's six-stage fifth-order method, b_i >= 0
+    t.s = 6;
+    t.a[1][0] = 0.25;
+    t.a[2][0] = 0.125;
+    t.a[2][1] = 0.125;
+    t.a[3][1] = -0.5;
+    t.a[3][2] = 1.0;
+    t.a[4][0] = 3.0 / 16.0;
+    t.a[4][3] = 9.0 / 16.0;
+    t.a[5][0] = -3.0 / 7.0;
+    t.a[5][1] = 2.0 / 7.0;
+    t.a[5][2] = 12.0 / 7.0;
+    t.a[5][3] = -12.0 / 7.0;
+    t.a[5][4] = 8.0 / 7.0;
+    t.c[1] = 0.25;
+    t.c[2] = 0.25;
+    t.c[3] = 0.5;
+    t.c[4] = 0.75;
+    t.c[5] = 1.0;
+    t.b[0] = 7.0 / 90.0;
+    t.b[2] = 32.0 / 90.0;
+    t.b[3] = 12.0 / 90.0;
+    t.b[4] = 32.0 / 90.0;
+    t.b[5] = 7.0 / 90.0;
   } else {  // classical RK(4,4)
     t.s = 4;
     t.a[1][0] = 0.5;
@@ -121,7 +146,7 @@ namespace es {
 int validate_config(const es_config& C) {
   if (C.p < 2 || C.p > 5 || C.nx < 1 || C.ny < 1 || C.nz < 1) return ES_ERR_INVALID;
   if (!(C.gamma_gas > 1.0) || !(C.R > 0.0) || C.mu < 0.0 || (C.mu > 0.0 && !(C.Pr > 0.0))) return ES_ERR_INVALID;
-  if (C.rk != ES_RK_BS3 && C.rk != ES_RK_RK4) return ES_ERR_INVALID;
+  if (C.rk != ES_RK_BS3 && C.rk != ES_RK_RK4 && C.rk != ES_RK_RK65) return ES_ERR_INVALID;
   if (C.precision < ES_FP64 || C.precision > ES_MIXED_FF) return ES_ERR_INVALID;
   if (!(C.visc_diss >= 0.0) || !std::isfinite(C.visc_diss)) return ES_ERR_INVALID;
   if (C.relax != ES_RELAX_NONE && C.relax != ES_RELAX_LOCAL && C.relax != ES_RELAX_GLOBAL) return ES_ERR_INVALID;
@@ -226,7 +251,8 @@ struct Group {
   int vol_variant = 0;
   std::vector<InstGeom> geom;      // host copy of the instance table
   std::vector<int> inst_ids;       // batch instance index of each local instance
-  void* k[4] = {nullptr, nullptr, nullptr, nullptr};  // stage values, tf bytes each
+  void* k[kMaxStages] = {};  // stage values, tf bytes each
+  int nk = 0;                // allocated stage buffers
   void* aux = nullptr;
   void* F = nullptr;
   void* fV = nullptr;
@@ -442,6 +468,7 @@ int group_init(Group& g, const es_config* insts, int n, int stages, bool own_sta
   const long long P2 = (long long)g.P1 * g.P1;
   int rc = ES_OK;
   for (int i = 0; i < stages && rc == ES_OK; ++i) rc = dev_alloc_bytes(&g.k[i], 5 * N * g.tf);
+  if (rc == ES_OK) g.nk = stages;
   if (rc == ES_OK) rc = dev_alloc_bytes(&g.aux, kAuxPlanes * N * g.tf);
   if (rc == ES_OK) rc = dev_alloc_bytes(&g.F, 15 * K * P2 * g.tf);
   if (rc == ES_OK && C.mu > 0.0) rc = dev_alloc_bytes(&g.fV, 12 * N * g.tf);
@@ -865,6 +892,41 @@ int es_set_boundary(es_ctx* c, int dir, int kind, const double* params, int npar
 int es_set_time(es_ctx* c, double t) {
   if (!c || !std::isfinite(t)) return ES_ERR_INVALID;
   return cuda_check(cudaMemcpy(c->g.t, &t, sizeof(double), cudaMemcpyHostToDevice));
+}
+
+int es_set_tableau(es_ctx* c, int s, const double* a, const double* b, const double* cs) {
+  if (!c || !a || !b || !cs || s < 1 || s > kMaxStages) return ES_ERR_INVALID;
+  Tableau t;
+  std::memset(&t, 0, sizeof(t));
+  double bsum = 0.0;
+  for (int i = 0; i < s; ++i) {
+    double row = 0.0;
+    for (int j = 0; j < s; ++j) {
+      const double v = a[i * s + j];
+      if (!std::isfinite(v) || (j >= i && v != 0.0)) return ES_ERR_INVALID;  // explicit: strictly lower
+      if (j < i) t.a[i][j] = v;
+      row += v;
+    }
+    if (!std::isfinite(b[i]) || !std::isfinite(cs[i])) return ES_ERR_INVALID;
+    // Eq. (eta-est-1-RK) bounds the entropy only for non-negative weights
+    if (c->eng.relax != ES_RELAX_NONE && b[i] < 0.0) return ES_ERR_INVALID;
+    if (std::fabs(row - cs[i]) > 1e-13 * (1.0 + std::fabs(cs[i]))) return ES_ERR_INVALID;
+    t.b[i] = b[i];
+    t.c[i] = cs[i];
+    bsum += b[i];
+  }
+  if (std::fabs(bsum - 1.0) > 1e-13) return ES_ERR_INVALID;
+  int se = s;
+  while (se > 0 && t.b[se - 1] == 0.0) --se;
+  t.s = se;
+  Group& g = c->g;
+  for (int i = g.nk; i < se; ++i) {
+    const int rc = dev_alloc_bytes(&g.k[i], 5 * g.N * g.tf);
+    if (rc != ES_OK) return rc;
+    g.nk = i + 1;
+  }
+  c->eng.tab = t;
+  return ES_OK;
 }
 
 int es_entropy(es_ctx* c, const double* q, double* eta, void* stream) {

@@ -275,7 +275,7 @@ __device__ __forceinline__ double to_f64(ff x) { return double(x); }
 
 // ---------------------------------------------------------------------------
 // y = u (+ gamma d when the instance has a pending relaxed update and this is the
-// step's first stage) + dt sum_j a_ij k_j; NPREV stages enter (compile time).
+// step's first stage) + dt sum_j a_ij k_j over the stages with a_ij != 0.
 // FP64 mode: everything in FP64.  Mixed mode with FP64 estimates (P.ff_est = 0):
 // e = dt sum_j a_ij k_j, y = u + e and w(y) - w(u) in FP64 (the FP32 k_j placed into
 // FP64 on the integer pipe); the parameter vector for the FP32 fluxes is formed from
@@ -283,6 +283,8 @@ __device__ __forceinline__ double to_f64(ff x) { return double(x); }
 // FP64 state is split into float-float (integer pipe), e, y, the parameter vector and
 // w(y) - w(u) are formed in float-float on the FP32 pipe.  FP64 selects the
 // FP64-increment paths at compile time (they differ widely in register use).
+// NPREV >= 0 fixes the number of earlier stages at compile time; NPREV < 0 reads it
+// from sp.nprev (tableaux with more than three nonzero a_ij in a row).
 template <typename TF, int NPREV, bool FP64>
 __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __restrict__ status) {
   const long long N = (long long)P.K * sp.Np;
@@ -302,10 +304,10 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
     }
     if constexpr (FP64 && !std::is_same<TF, double>::value) {
       double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      if constexpr (NPREV > 0) {
+      if constexpr (NPREV != 0) {
         const double dt = geom_of(P, inst).dt;
 #pragma unroll
-        for (int j = 0; j < NPREV; ++j) {
+        for (int j = 0; j < (NPREV >= 0 ? NPREV : sp.nprev); ++j) {
           const double c = sp.coef[j] * dt;
           const TF* kj = static_cast<const TF*>(sp.k[j]);
 #pragma unroll
@@ -328,10 +330,10 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
       double y[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) y[v] = u[v];
-      if constexpr (NPREV > 0) {
+      if constexpr (NPREV != 0) {
         const double dt = geom_of(P, inst).dt;
 #pragma unroll
-        for (int j = 0; j < NPREV; ++j) {
+        for (int j = 0; j < (NPREV >= 0 ? NPREV : sp.nprev); ++j) {
           const double c = sp.coef[j] * dt;
           const double* kj = static_cast<const double*>(sp.k[j]);
 #pragma unroll
@@ -368,10 +370,10 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
         uf[v] = ff_from_double(u[v]);
         ef[v] = ff(0.0f, 0.0f);
       }
-      if constexpr (NPREV > 0) {
+      if constexpr (NPREV != 0) {
         const double dt = geom_of(P, inst).dt;
 #pragma unroll
-        for (int j = 0; j < NPREV; ++j) {
+        for (int j = 0; j < (NPREV >= 0 ? NPREV : sp.nprev); ++j) {
           const ff c = ff_from_double(sp.coef[j] * dt);
           const TF* kj = static_cast<const TF*>(sp.k[j]);
 #pragma unroll
@@ -1421,7 +1423,8 @@ void prep_launch(const Params& P, const StagePrep& sp, TF* a, int* status, cudaS
     case 0: k_prep<TF, 0, FP64><<<grid, 256, 0, st>>>(P, sp, a, status); break;
     case 1: k_prep<TF, 1, FP64><<<grid, 256, 0, st>>>(P, sp, a, status); break;
     case 2: k_prep<TF, 2, FP64><<<grid, 256, 0, st>>>(P, sp, a, status); break;
-    default: k_prep<TF, 3, FP64><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+    case 3: k_prep<TF, 3, FP64><<<grid, 256, 0, st>>>(P, sp, a, status); break;
+    default: k_prep<TF, -1, FP64><<<grid, 256, 0, st>>>(P, sp, a, status); break;
   }
 }
 

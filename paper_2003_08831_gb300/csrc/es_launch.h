@@ -14,6 +14,9 @@ InstGeom instance_geom(const es_config& C, int off);
 void build_params(const es_config& C, Params* out);
 int grid_for_sms(int sm_count, long long n, int block);
 
+// explicit Runge--Kutta tableaux of up to kMaxStages stages
+constexpr int kMaxStages = 10;
+
 // k_prep: stage state y = u (+ gamma d first) + dt sum_j coef[j] k[j]
 struct StagePrep {
   double* q;                // u, updated in place when an update is pending
@@ -21,8 +24,8 @@ struct StagePrep {
   const double* gamma_cur;  // per instance: gamma of the previous step
   const int* pending;       // per instance: relaxed update u += gamma d not yet applied (nullptr: none)
   int nprev;
-  double coef[4];           // a_ij (multiplied by the instance's dt in the kernel)
-  const void* k[4];         // stage values in the flux precision (double, float or float-float)
+  double coef[kMaxStages];  // a_ij (multiplied by the instance's dt in the kernel)
+  const void* k[kMaxStages];  // stage values in the flux precision (double, float or float-float)
   double* dw;               // w(y) - w(u) output, or nullptr
   int Np;
 };
@@ -33,8 +36,8 @@ struct StageVol {
   double* kout64;      // k_i = f(y^i) in FP64 (the right-hand-side entry points)
   double* d_out;       // last stage: d = dt (dcoef_self k_i + sum_j dcoef[j] dk[j]) instead of k_i
   int nd;
-  double dcoef[4];     // b_j
-  const void* dk[4];   // earlier stages' k in the flux precision
+  double dcoef[kMaxStages];    // b_j
+  const void* dk[kMaxStages];  // earlier stages' k in the flux precision
   double dcoef_self;   // b_i
   double* E;           // (eta' f)(y^i) per element, or nullptr
   const double* dw;    // w(y^i) - w(u), or nullptr

@@ -150,6 +150,10 @@ class Solver:
         """Time at which rhs() evaluates prescribed boundary states."""
         B.es_set_time(self.ctx, t)
 
+    def set_tableau(self, A, b, c):
+        """Explicit Runge--Kutta tableau (up to 10 stages) for the following steps."""
+        B.es_set_tableau(self.ctx, A, b, c)
+
     def autotune(self, q, stream=None):
         B.es_autotune(self.ctx, q, stream)
 

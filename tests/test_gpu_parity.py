@@ -154,7 +154,7 @@ def compare_advance(mesh, U, lo, hi, phys, tabname, nsteps, mode="local", cfl=0.
     sens_g, sens_gk = gamma_sensitivity(mesh, U, dt, nsteps, phys, rk.TABLEAUX[tabname], mode, hist, eps=eps)
     relax_mode = {"local": B.ES_RELAX_LOCAL, "global": B.ES_RELAX_GLOBAL, "none": B.ES_RELAX_NONE}[mode]
     s = solver(mesh.p, mesh.n, lo, hi, mu=phys.mu, Pr=phys.Pr, interface_diss=phys.diss,
-               rk=B.ES_RK_BS3 if tabname == "BS3" else B.ES_RK_RK4, relax=relax_mode,
+               rk={"BS3": B.ES_RK_BS3, "RK4": B.ES_RK_RK4, "RK65": B.ES_RK_RK65}[tabname], relax=relax_mode,
                visc_diss=phys.visc_diss, **kw)
     q = s.to_device(U)
     t, gh, gk = s.advance(q, nsteps, dt)
@@ -525,4 +525,84 @@ def test_advance_viscous_interface_dissipation():
     mesh = dg.Mesh(3, (3, 3, 3), lo, hi)
     U = random_state(mesh, seed=77, noise=0.01)
     compare_advance(mesh, U, lo, hi, dg.Physics(G, mu=0.01, Pr=0.72, diss=1, visc_diss=1.0), "BS3", 5)
+
+
+# ---------------------------------------------------------------------------------------
+# fifth-order tableau (RK(6,5), b >= 0) and caller-supplied tableaux (es_set_tableau)
+
+@pytest.mark.parametrize("mode", ["local", "global"])
+def test_advance_rk65(mode):
+    mesh, U, lo, hi = vortex_setup(N=4, p=4, nz=1)
+    g = compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=1), "RK65", 8, mode=mode)
+    assert np.all(np.abs(g - 1) < 0.1)
+
+
+def test_advance_rk65_navier_stokes():
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    mesh = dg.Mesh(3, (3, 3, 3), lo, hi)
+    U = random_state(mesh, seed=91, noise=0.01)
+    compare_advance(mesh, U, lo, hi, dg.Physics(G, mu=0.01, Pr=0.72, diss=1), "RK65", 4)
+
+
+def _run(p, n, lo, hi, U, dt, nsteps, rkc, tab=None):
+    s = solver(p, n, lo, hi, rk=rkc)
+    if tab is not None:
+        s.set_tableau(tab["A"], tab["b"], tab["c"])
+    q = s.to_device(U)
+    t, gh, gk = s.advance(q, nsteps, dt)
+    assert s.status() == 0
+    out = (q.cpu().numpy(), t.item(), gh.cpu().numpy(), gk.cpu().numpy())
+    s.close()
+    return out
+
+
+def test_set_tableau_reproduces_builtin_and_oracle():
+    """A tableau loaded through es_set_tableau runs the same kernels as the built-in one
+    (bit-identical states, gamma and t); a 7-stage tableau with a trailing zero weight
+    (RK65 with an unused last stage) is identical too; a 3-stage method loaded into a
+    context created with RK(4,4) matches the oracle."""
+    from paper_2003_08831_gb300 import _binding as B
+    mesh, U, lo, hi = vortex_setup(N=4, p=3, nz=1)
+    phys = dg.Physics(G, diss=1)
+    dt = rk.stable_dt(mesh, U, phys, 0.5)
+    ref = _run(3, mesh.n, lo, hi, U, dt, 5, B.ES_RK_RK65)
+    got = _run(3, mesh.n, lo, hi, U, dt, 5, B.ES_RK_BS3, rk.RK65)
+    for a, b in zip(ref, got):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+    t7 = {"A": np.zeros((7, 7)), "b": np.zeros(7), "c": np.zeros(7)}
+    t7["A"][:6, :6] = rk.RK65["A"]
+    t7["A"][6, :6] = rk.RK65["b"]
+    t7["b"][:6] = rk.RK65["b"]
+    t7["c"][:6] = rk.RK65["c"]
+    t7["c"][6] = 1.0
+    got7 = _run(3, mesh.n, lo, hi, U, dt, 5, B.ES_RK_RK4, t7)
+    for a, b in zip(ref, got7):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+    Uo, to, hist = rk.advance(mesh, U, dt, 5, phys, rk.BS3)
+    q, t, gh, _ = _run(3, mesh.n, lo, hi, U, dt, 5, B.ES_RK_RK4, rk.BS3)
+    assert np.all(rel_err_per_var(q, Uo) < TOL)
+    assert abs(t - to) < 1e-12 * to
+
+
+def test_set_tableau_rejects_invalid():
+    from paper_2003_08831_gb300 import _binding as B
+    s = solver(3, (2, 2, 2), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    A, b, c = rk.RK4["A"].copy(), rk.RK4["b"].copy(), rk.RK4["c"].copy()
+    bad = []
+    A1 = A.copy()
+    A1[1, 2] = 0.1                                    # implicit entry
+    bad.append((A1, b, c))
+    bad.append((A, b * 1.01, c))                      # sum b != 1
+    c1 = c.copy()
+    c1[2] = 0.6                                       # row sum != c
+    bad.append((A, b, c1))
+    b1 = np.array([0.25, 0.5, 0.5, -0.25])            # negative weight with relaxation on
+    bad.append((A, b1, c))
+    bad.append((np.zeros((11, 11)), np.full(11, 1.0 / 11), np.zeros(11)))   # more than 10 stages
+    for A_, b_, c_ in bad:
+        with pytest.raises(B.ESError):
+            s.set_tableau(A_, b_, c_)
+    s.set_tableau(A, b, c)                            # still usable
+    assert s.status() == 0
+    s.close()
 

@@ -10,6 +10,7 @@
 * Section 4.4 (Eq. visu_of_local_gamma): |gamma_kappa - 1| < 2e-5 (golden file).
 * Section 4.1.1: design-order convergence on the isentropic vortex.
 """
+import itertools
 import os
 
 import numpy as np
@@ -152,7 +153,7 @@ def test_local_inequality_and_conservation():
         U = res.U
 
 
-@pytest.mark.parametrize("tabname,q", [("BS3", 3), ("RK4", 4)])
+@pytest.mark.parametrize("tabname,q", [("BS3", 3), ("RK4", 4), ("RK65", 5)])
 def test_gamma_minus_one_order(tabname, q):
     """Lemma 2.1: max |gamma_kappa - 1| shrinks like dt^(q-1)."""
     mesh, U = vortex_case(N=4, p=3, nz=1)
@@ -183,6 +184,60 @@ def test_order_conditions(tabname):
         assert abs(b @ (c * (A @ c)) - 1 / 8) < 1e-15
         assert abs(b @ A @ c ** 2 - 1 / 12) < 1e-15
         assert abs(b @ A @ A @ c - 1 / 24) < 1e-15
+
+
+def _rooted_trees(n):
+    """All rooted trees with n nodes, each a sorted tuple of its subtrees."""
+    if n == 1:
+        return [()]
+    out = set()
+
+    def partitions(m, largest):
+        if m == 0:
+            yield []
+            return
+        for k in range(min(m, largest), 0, -1):
+            for rest in partitions(m - k, k):
+                yield [k] + rest
+    for part in partitions(n - 1, n - 1):
+        for combo in itertools.product(*[_rooted_trees(k) for k in part]):
+            out.add(tuple(sorted(combo)))
+    return sorted(out)
+
+
+def _density(t):
+    n = 1 + sum(_size(c) for c in t)
+    for c in t:
+        n *= _density(c)
+    return n
+
+
+def _size(t):
+    return 1 + sum(_size(c) for c in t)
+
+
+def _stage_weights(t, A):
+    """Per-stage product over the root's subtrees of A (their stage weights)."""
+    v = np.ones(A.shape[0])
+    for c in t:
+        v = v * (A @ _stage_weights(c, A))
+    return v
+
+
+@pytest.mark.parametrize("tabname", ["BS3", "RK4", "RK65"])
+def test_order_conditions_rooted_trees(tabname):
+    """Butcher's conditions b . Phi(t) = 1/gamma(t) for every rooted tree t with at most
+    `order` nodes (1, 1, 2, 4, 9 trees of orders 1..5), failing for some tree of order + 1,
+    and b_i >= 0 (Example 2.5)."""
+    t = rk.TABLEAUX[tabname]
+    A, b, q = t["A"], t["b"], t["order"]
+    assert np.all(b >= 0) and np.all(np.triu(A) == 0)
+    assert [len(_rooted_trees(n)) for n in range(1, 7)] == [1, 1, 2, 4, 9, 20]
+    for n in range(1, q + 1):
+        for tree in _rooted_trees(n):
+            assert abs(b @ _stage_weights(tree, A) - 1.0 / _density(tree)) < 1e-14, (n, tree)
+    worst = max(abs(b @ _stage_weights(tree, A) - 1.0 / _density(tree)) for tree in _rooted_trees(q + 1))
+    assert worst > 1e-6
 
 
 def read_golden(name):
