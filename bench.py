@@ -105,7 +105,7 @@ def kernel_flops(p, n_el, stages=3):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_volume launch of the
 # default workload, from the ncu capture summarised in profiles/ (stage 3 of a step, FP64).
 # It is reported only while the kernel sources hash to the value the capture was taken with.
-VOLUME_TRAFFIC = {"source_sha1": "424b9f041b2902d328ea9812e7cbd6081afe0884", "bytes_per_launch": 399509760 + 67806208}
+VOLUME_TRAFFIC = {"source_sha1": "ff68496622ce3c8c17321cdad8c43af83d9f8b25", "bytes_per_launch": 399829760 + 67920128}
 
 
 def kernel_source_sha1():

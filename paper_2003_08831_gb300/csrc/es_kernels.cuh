@@ -167,11 +167,13 @@ __device__ __forceinline__ void entropy_var_increment_ff(const ff u[5], const ff
 // Lanes per element in the relaxation kernels: a group of SUB lanes solves one element,
 // so for Np <= 64 two or four elements share a warp and the per-element scalar work
 // (reductions, bracket and Newton logic, executed by every lane of the group) is paid
-// once per 16 or 8 lanes instead of once per warp.
-template <int P1>
+// once per 16 or 8 lanes instead of once per warp.  The float-float solve (FF) holds
+// twice the registers per node value and is latency-bound: it takes whole warps from
+// Np > 32 on (measured: 1 % faster for p = 3, where the FP64 solve is 1 % slower).
+template <int P1, bool FF = false>
 struct RelaxGroup {
   static constexpr int Np = P1 * P1 * P1;
-  static constexpr int SUB = Np <= 32 ? 8 : (Np <= 64 ? 16 : 32);
+  static constexpr int SUB = Np <= 32 ? 8 : ((Np <= 64 && !FF) ? 16 : 32);
   static constexpr int R = (Np + SUB - 1) / SUB;  // nodes per lane
   static constexpr int EPW = 32 / SUB;            // elements per warp
   static __device__ __forceinline__ unsigned mask(int lane) {
@@ -1094,7 +1096,7 @@ __device__ __forceinline__ ff ff_max(ff x, ff y) { return x < y ? y : x; }
 
 template <int P1>
 __global__ void k_relax_ff(Params P, StageRelax sr) {
-  using RG = RelaxGroup<P1>;
+  using RG = RelaxGroup<P1, true>;
   constexpr int Np = RG::Np, R = RG::R, SUB = RG::SUB;
   const long long N = (long long)P.K * Np;
   const FluxConst<ff>& C = P.Cff;
@@ -1510,11 +1512,12 @@ void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* a
 template <int P1, typename TF>
 void Launcher<P1, TF>::relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid) {
   // the u_new entry point (es_relax_step), the FP64 mode and the mixed mode with FP64
-  // estimates solve in FP64; 4 warps per block, RelaxGroup<P1>::EPW elements per warp
-  const int need = (P.K + 4 * RelaxGroup<P1>::EPW - 1) / (4 * RelaxGroup<P1>::EPW);
+  // estimates solve in FP64; 4 warps per block, RelaxGroup::EPW elements per warp
+  const bool fp64 = sr.u_new || std::is_same<TF, double>::value || (std::is_same<TF, float>::value && !P.ff_est);
+  const int epb = 4 * (fp64 ? RelaxGroup<P1>::EPW : RelaxGroup<P1, true>::EPW);
+  const int need = (P.K + epb - 1) / epb;
   const int g = grid < need ? grid : need;
-  if (sr.u_new || std::is_same<TF, double>::value || (std::is_same<TF, float>::value && !P.ff_est))
-    k_relax<P1><<<g, 128, 0, st>>>(P, sr);
+  if (fp64) k_relax<P1><<<g, 128, 0, st>>>(P, sr);
   else k_relax_ff<P1><<<g, 128, 0, st>>>(P, sr);
 }
 
