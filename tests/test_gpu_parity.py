@@ -606,3 +606,70 @@ def test_set_tableau_rejects_invalid():
     assert s.status() == 0
     s.close()
 
+
+# ---------------------------------------------------------------------------------------
+# mixed modes at full size (32^3 TGV): sampled elements against oracle element blocks,
+# bars in the FP32 rounding unit
+
+EPS32 = 2.0 ** -23
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("p,mu,noise", [(3, 0.0, False), (4, 1.0 / 1600.0, True)])
+def test_mixed_full_size_rhs_sampled(p, mu, noise, prec):
+    """Euler TGV (config 2) and the noisy Navier--Stokes TGV (config 4) with FP32 fluxes:
+    es_rhs per node within 256 eps_32 of the summed term magnitudes of the oracle."""
+    mesh, U, lo, hi = tgv_full(p, noise=noise)
+    phys = dg.Physics(G, mu=mu, Pr=0.72, diss=1)
+    s = solver(p, mesh.n, lo, hi, mu=mu, precision=prec)
+    dq = s.rhs(s.to_device(U)).cpu().numpy().reshape(mesh.shape)
+    assert s.status() == 0
+    s.close()
+    radius = 2 if mu > 0 else 1
+    nb = 2 * radius + 1
+    bm = dg.Mesh(p, (nb, nb, nb), (0, 0, 0), tuple(nb * h for h in mesh.h))
+    for c in SAMPLES[:3]:
+        B = dg.element_block(U, c, radius)
+        ref = dg.rhs(bm, B, phys)[:, radius, radius, radius]
+        terms = dg.rhs_term_magnitude(bm, B, phys)[:, radius, radius, radius]
+        assert_rhs_close(dq[:, c[2], c[1], c[0]], ref, terms, eps=EPS32)
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_mixed_full_size_step_sampled(prec):
+    """One relaxed BS3 step of the 32^3 p = 3 Euler TGV with FP32 fluxes: gamma_kappa of
+    sampled elements within 8x its response to FP32-level changes of the right-hand
+    side, and q_new - q_old = gamma d within the FP32 rounding of the stage sums."""
+    p = 3
+    mesh, U, lo, hi = tgv_full(p)
+    phys = dg.Physics(G, diss=1)
+    dt = rk.stable_dt(mesh, U, phys, 0.5)
+    s = solver(p, mesh.n, lo, hi, precision=prec)
+    q = s.to_device(U)
+    t, gh, gk = s.advance(q, 1, dt)
+    assert s.status() == 0
+    qn = q.cpu().numpy().reshape(mesh.shape)
+    gk = gk.cpu().numpy().reshape(mesh.n[2], mesh.n[1], mesh.n[0])
+    gamma = gh.cpu().numpy()[0]
+    s.close()
+    assert gamma == np.min(gk)
+    radius = 3
+    nb = 2 * radius + 1
+    bm = dg.Mesh(p, (nb, nb, nb), (0, 0, 0), tuple(nb * h for h in mesh.h))
+    for c in SAMPLES[:3]:
+        B = dg.element_block(U, c, radius)
+        r = rk.rk_step(bm, B, dt, phys, rk.BS3, delta_floor=4e-6)
+        g_ref = r.gamma_kappa[radius, radius, radius]
+        _, sens = gamma_sensitivity(bm, B, dt, 1, phys, rk.BS3, "local", [r], seeds=2, eps=EPS32)
+        tol = max(1e-6, 8 * sens.reshape(nb, nb, nb)[radius, radius, radius])
+        g_got = gk[c[2], c[1], c[0]]
+        if np.isinf(g_ref):        # change below the floor: unconstrained on both sides
+            assert np.isinf(g_got), (c, g_got)
+        else:
+            assert abs(g_got - g_ref) <= tol * g_ref, (c, g_got, g_ref, tol)
+        d_ref = r.d[:, radius, radius, radius]
+        d_got = (qn[:, c[2], c[1], c[0]] - U[:, c[2], c[1], c[0]]) / gamma
+        terms = dg.rhs_term_magnitude(bm, B, phys)[:, radius, radius, radius]
+        bound = 1e-6 * np.max(np.abs(d_ref)) + dt * 256 * EPS32 * terms + 4 * EPS * np.abs(U[:, c[2], c[1], c[0]])
+        assert np.all(np.abs(d_got - d_ref) <= bound)
+
