@@ -124,7 +124,8 @@ class Solver:
         c = self.cfg
         return {"p": c.p, "n": [c.nx, c.ny, c.nz], "lo": list(c.lo), "hi": list(c.hi), "gamma_gas": c.gamma_gas,
                 "mu": c.mu, "Pr": c.Pr, "R": c.R, "interface_diss": c.interface_diss, "relax": c.relax,
-                "rk": c.rk, "precision": c.precision, "delta_floor": c.delta_floor, "visc_diss": c.visc_diss}
+                "rk": c.rk, "precision": c.precision, "delta_floor": c.delta_floor, "visc_diss": c.visc_diss,
+                "tableau": getattr(self, "tableau", None)}
 
     def checkpoint(self, path, q, t, step, dt):
         """Write the device state q, time t (float) and step counter to path (see save_checkpoint)."""
@@ -139,6 +140,8 @@ class Solver:
         s = cls(c["p"], tuple(c["n"]), tuple(c["lo"]), tuple(c["hi"]), c["gamma_gas"], c["mu"], c["Pr"], c["R"],
                 c["interface_diss"], c["relax"], c["rk"], c["precision"], c["delta_floor"], device=device,
                 visc_diss=c.get("visc_diss", 0.0))
+        if c.get("tableau"):
+            s.set_tableau(c["tableau"]["A"], c["tableau"]["b"], c["tableau"]["c"])
         return s, s.to_device(q), h["t"], h["step"], h["dt"]
 
     def set_boundary(self, direction, kind, params=None):
@@ -151,8 +154,11 @@ class Solver:
         B.es_set_time(self.ctx, t)
 
     def set_tableau(self, A, b, c):
-        """Explicit Runge--Kutta tableau (up to 10 stages) for the following steps."""
+        """Explicit Runge--Kutta tableau (up to 10 stages) for the following steps; it is
+        stored with checkpoints."""
         B.es_set_tableau(self.ctx, A, b, c)
+        self.tableau = {"A": [list(map(float, row)) for row in A], "b": list(map(float, b)),
+                        "c": list(map(float, c))}
 
     def autotune(self, q, stream=None):
         B.es_autotune(self.ctx, q, stream)

@@ -22,14 +22,21 @@ def test_checkpoint_file_round_trip(tmp_path):
 
 
 @pytest.mark.gpu
-def test_resume_is_bit_identical(tmp_path):
+@pytest.mark.parametrize("tableau", [None, "RK65"])
+def test_resume_is_bit_identical(tmp_path, tableau):
+    """Also with a tableau loaded through set_tableau, which the checkpoint carries."""
     import torch
+
+    from oracle import rk
 
     import __graft_entry__
     __graft_entry__.build()
     from paper_2003_08831_gb300.solver import Solver, stable_dt
     lo, hi = (0.0, 0.0, 0.0), (10.0, 10.0, 10.0)
     s = Solver(3, (4, 3, 5), lo, hi)
+    if tableau:
+        tab = rk.TABLEAUX[tableau]
+        s.set_tableau(tab["A"], tab["b"], tab["c"])
     xyz = s.coords()
     q0 = inputs.vortex_state(xyz[0], xyz[1], 0.0, centre=(5.0, 5.0), period=10.0)
     dt = stable_dt(q0, 3, [2.5, 10 / 3, 2.0], 0.5)
