@@ -86,6 +86,10 @@ def volume_flops_per_element(p, ns=False, with_A=False):
 #   update in the first stage); entropy-variable increments 131 in stages 2 and 3;
 # k_relax per node and step: setup 85 (primitive state 35, X0 Y0 V2 25, a and the cubic
 #   coefficient 25) + 75 per Bregman evaluation (one for a smooth step from the cubic start).
+# k_grad per node (Navier--Stokes): entropy variables from z 4; per direction the D product
+#   8 (p+1), the metric 4 and the face lifting 12 on the 2/(p+1) face nodes; chain rule 90
+#   (velocity 3, 1/w_5 1, velocity gradients 27, temperature gradients 9, divergence 2,
+#   stresses 27, energy fluxes 21).
 FACE_FLOPS_PER_FACE_NODE = 56 + 55
 PREP_FLOPS_Z, PREP_FLOPS_PER_STAGE, PREP_FLOPS_PENDING, PREP_FLOPS_DW = 22, 10, 10, 131
 RELAX_FLOPS_SETUP, RELAX_FLOPS_EVAL = 85, 75
@@ -99,13 +103,14 @@ def kernel_flops(p, n_el, stages=3):
                     + sum(PREP_FLOPS_PER_STAGE * i + (PREP_FLOPS_DW if i > 0 else 0) for i in range(stages))) / stages
     face = 3 * n_el * P1 * P1 * FACE_FLOPS_PER_FACE_NODE
     relax = nodes * (RELAX_FLOPS_SETUP + RELAX_FLOPS_EVAL)
-    return {"prep": prep, "face": face, "relax": relax}
+    grad = nodes * (4 + 3 * (8 * P1 + 4 + 24.0 / P1) + 90)
+    return {"prep": prep, "face": face, "relax": relax, "grad": grad}
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_volume launch of the
 # default workload, from the ncu capture summarised in profiles/ (stage 3 of a step, FP64).
 # It is reported only while the kernel sources hash to the value the capture was taken with.
-VOLUME_TRAFFIC = {"source_sha1": "ff68496622ce3c8c17321cdad8c43af83d9f8b25", "bytes_per_launch": 399829760 + 67920128}
+VOLUME_TRAFFIC = {"source_sha1": "3d87c7d28eb6720adf6e80c37d4cbfad7583acd2", "bytes_per_launch": 399743488 + 68273408}
 
 
 def kernel_source_sha1():
@@ -411,9 +416,11 @@ def measure_shock(precision, steps=50, warmup=3, n=25, p=3):
 def kernel_roofline(p, n_el, wl, prof, peak, vol_flops):
     """Per kernel kind: algorithmic flops per launch / average event-timed launch, as a
     fraction of the ALU peak (FP64 workloads; other precisions report null)."""
-    if wl["precision"] != 0 or wl["mu"] > 0:
+    if wl["precision"] != 0:
         return None
     fl = kernel_flops(p, n_el)
+    if wl["mu"] == 0.0:
+        del fl["grad"]
     fl["volume"] = vol_flops
     out = {}
     for k, f in fl.items():
@@ -627,6 +634,12 @@ def run_full(args, rank, world, local_rank):
                            "speedup_vs_fp64_same_physics": None}
             if err is not None:
                 forms[name]["error_vs_fp64"] = err
+            if w2["precision"] == 0:      # per-kernel fractions of the FP64 ALU peak
+                n2 = w2["n"] ** 3
+                ns2 = w2["mu"] > 0
+                vf = n2 * (volume_flops_per_element(w2["p"], ns2, False)
+                           + 2 * volume_flops_per_element(w2["p"], ns2, True)) / 3.0
+                forms[name]["kernel_roofline"] = kernel_roofline(w2["p"], n2, w2, p2, peak, vf)
             del r2
         forms["viscous_shock_ns_p3_25^3_fp64"] = measure_shock(0)
         forms["viscous_shock_ns_p3_25^3_fp64x"] = measure_shock(2)

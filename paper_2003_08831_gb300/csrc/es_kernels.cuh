@@ -165,15 +165,17 @@ __device__ __forceinline__ void entropy_var_increment_ff(const ff u[5], const ff
 }
 
 // Lanes per element in the relaxation kernels: a group of SUB lanes solves one element,
-// so for Np <= 64 two or four elements share a warp and the per-element scalar work
+// so for small Np two or four elements share a warp and the per-element scalar work
 // (reductions, bracket and Newton logic, executed by every lane of the group) is paid
-// once per 16 or 8 lanes instead of once per warp.  The float-float solve (FF) holds
-// twice the registers per node value and is latency-bound: it takes whole warps from
-// Np > 32 on (measured: 1 % faster for p = 3, where the FP64 solve is 1 % slower).
+// once per 16 or 8 lanes instead of once per warp.  The FP64 solve keeps 16-lane groups
+// up to p = 4 (8 nodes per lane there; 4 % faster than whole warps).  The float-float
+// solve (FF) holds twice the registers per node value and is latency-bound: it takes
+// whole warps from Np > 32 on (measured: 1 % faster for p = 3, where the FP64 solve is
+// 1 % slower).
 template <int P1, bool FF = false>
 struct RelaxGroup {
   static constexpr int Np = P1 * P1 * P1;
-  static constexpr int SUB = Np <= 32 ? 8 : ((Np <= 64 && !FF) ? 16 : 32);
+  static constexpr int SUB = Np <= 32 ? 8 : ((Np <= 128 && !FF) ? 16 : 32);
   static constexpr int R = (Np + SUB - 1) / SUB;  // nodes per lane
   static constexpr int EPW = 32 / SUB;            // elements per warp
   static __device__ __forceinline__ unsigned mask(int lane) {
