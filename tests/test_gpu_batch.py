@@ -149,3 +149,34 @@ def test_single_context_autotune_keeps_results():
     torch.cuda.synchronize()
     assert torch.equal(r0, r1)
     s.close()
+
+
+def test_batch_rk65_equals_single_contexts():
+    """The fifth-order RK(6,5) (rows of up to five earlier stages: the run-time stage count
+    of the stage preparation) inside the captured batch graph: bit-identical to each
+    instance alone in its own context."""
+    from paper_2003_08831_gb300 import _binding as B
+    from paper_2003_08831_gb300.solver import BatchSolver, Solver
+    insts = instances(4, seed=31)
+    nsteps = 3
+    b = BatchSolver(insts, rk=B.ES_RK_RK65)
+    dts = []
+    for i, inst in enumerate(insts):
+        mesh = dg.Mesh(inst["p"], inst["n"], inst["lo"], inst["hi"])
+        xyz = b.coords(i)
+        q0 = initial(inst, xyz[0], xyz[1])
+        b.set_state(i, q0)
+        dts.append(rk.stable_dt(mesh, mesh.unflat(q0), dg.Physics(G, diss=1), 0.5))
+    b.set_dt(dts)
+    b.advance(nsteps)
+    assert b.status() == 0
+    for i, inst in enumerate(insts):
+        s = Solver(inst["p"], inst["n"], inst["lo"], inst["hi"], rk=B.ES_RK_RK65)
+        xyz = s.coords()
+        q = s.to_device(initial(inst, xyz[0], xyz[1]))
+        s.advance(q, nsteps, dts[i])
+        assert s.status() == 0
+        assert np.array_equal(q.cpu().numpy(), b.get_state(i))
+        s.close()
+    b.close()
+
