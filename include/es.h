@@ -256,6 +256,9 @@ int es_batch_get_state(es_batch* b, int inst, double* q_host);
 int es_batch_set_dt(es_batch* b, const double* dt_host);
 /* tile autotuning per degree group on the current states (invalidates the graph) */
 int es_batch_autotune(es_batch* b, void* stream);
+/* es_set_tableau for every instance of the batch (same arguments and errors;
+ * synchronises the device and invalidates the graph) */
+int es_batch_set_tableau(es_batch* b, int s, const double* a, const double* bw, const double* c);
 /* the volume tile variant chosen for instance inst's group */
 int es_batch_volume_variant(const es_batch* b, int inst);
 /* nsteps relaxed steps of every instance (graph replay), ordered after prior

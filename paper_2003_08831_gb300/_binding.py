@@ -29,7 +29,8 @@ EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "
            "es_autotune", "es_batch_create", "es_batch_destroy", "es_batch_nodes", "es_batch_node_coords",
            "es_batch_set_state", "es_batch_get_state", "es_batch_set_dt", "es_batch_autotune",
            "es_batch_volume_variant", "es_batch_advance", "es_batch_times", "es_batch_status",
-           "es_batch_launch_count", "es_reciprocal", "es_set_boundary", "es_set_time", "es_set_tableau"]
+           "es_batch_launch_count", "es_reciprocal", "es_set_boundary", "es_set_time", "es_set_tableau",
+           "es_batch_set_tableau"]
 KERNEL_KINDS = ["prep", "face", "grad", "volume", "relax", "other"]
 
 
@@ -125,6 +126,8 @@ def load(path=None):
     lib.es_set_time.restype = i
     lib.es_set_tableau.argtypes = [vp, i, vp, vp, vp]
     lib.es_set_tableau.restype = i
+    lib.es_batch_set_tableau.argtypes = [vp, i, vp, vp, vp]
+    lib.es_batch_set_tableau.restype = i
     lib.es_strerror.argtypes = [i]
     lib.es_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -214,8 +217,7 @@ def es_set_time(ctx, t):
     _check(load().es_set_time(ctx, float(t)), "es_set_time")
 
 
-def es_set_tableau(ctx, A, b, c):
-    """A (s x s, strictly lower triangular), b, c: host sequences of floats."""
+def _tableau_arrays(A, b, c):
     import numpy as np
     A = np.ascontiguousarray(A, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -223,7 +225,19 @@ def es_set_tableau(ctx, A, b, c):
     s = b.size
     if A.shape != (s, s) or c.size != s:
         raise ValueError("tableau shapes: A (s, s), b (s,), c (s,)")
+    return s, A, b, c
+
+
+def es_set_tableau(ctx, A, b, c):
+    """A (s x s, strictly lower triangular), b, c: host sequences of floats."""
+    s, A, b, c = _tableau_arrays(A, b, c)
     _check(load().es_set_tableau(ctx, s, A.ctypes.data, b.ctypes.data, c.ctypes.data), "es_set_tableau")
+
+
+def es_batch_set_tableau(batch, A, b, c):
+    s, A, b, c = _tableau_arrays(A, b, c)
+    _check(load().es_batch_set_tableau(batch, s, A.ctypes.data, b.ctypes.data, c.ctypes.data),
+           "es_batch_set_tableau")
 
 
 def es_relax_step(ctx, u_old, u_new, d_eta, gamma_elem, gamma, u_out, stream=None):

@@ -451,6 +451,47 @@ void group_free(Group& g) {
   g = Group();
 }
 
+// A caller's explicit tableau (es_set_tableau, es_batch_set_tableau): a[i*s + j] strictly
+// lower triangular, sum_j a_ij = c_i, sum_i b_i = 1, b_i >= 0 when relaxing (Eq.
+// (eta-est-1-RK)); trailing stages with b_i = 0 dropped.
+int parse_tableau(int relax, int s, const double* a, const double* b, const double* cs, Tableau* out) {
+  if (!a || !b || !cs || !out || s < 1 || s > kMaxStages) return ES_ERR_INVALID;
+  Tableau t;
+  std::memset(&t, 0, sizeof(t));
+  double bsum = 0.0;
+  for (int i = 0; i < s; ++i) {
+    double row = 0.0;
+    for (int j = 0; j < s; ++j) {
+      const double v = a[i * s + j];
+      if (!std::isfinite(v) || (j >= i && v != 0.0)) return ES_ERR_INVALID;
+      if (j < i) t.a[i][j] = v;
+      row += v;
+    }
+    if (!std::isfinite(b[i]) || !std::isfinite(cs[i])) return ES_ERR_INVALID;
+    if (relax != ES_RELAX_NONE && b[i] < 0.0) return ES_ERR_INVALID;
+    if (std::fabs(row - cs[i]) > 1e-13 * (1.0 + std::fabs(cs[i]))) return ES_ERR_INVALID;
+    t.b[i] = b[i];
+    t.c[i] = cs[i];
+    bsum += b[i];
+  }
+  if (std::fabs(bsum - 1.0) > 1e-13) return ES_ERR_INVALID;
+  int se = s;
+  while (se > 0 && t.b[se - 1] == 0.0) --se;
+  t.s = se;
+  *out = t;
+  return ES_OK;
+}
+
+// Stage buffers for an s-stage tableau (allocated on first need, kept).
+int ensure_stage_buffers(Group& g, int s) {
+  for (int i = g.nk; i < s; ++i) {
+    const int rc = dev_alloc_bytes(&g.k[i], 5 * g.N * g.tf);
+    if (rc != ES_OK) return rc;
+    g.nk = i + 1;
+  }
+  return ES_OK;
+}
+
 // Allocates a group for the instances `insts` (same degree and physics).
 int group_init(Group& g, const es_config* insts, int n, int stages, bool own_state) {
   const es_config& C = insts[0];
@@ -904,38 +945,12 @@ int es_set_time(es_ctx* c, double t) {
 }
 
 int es_set_tableau(es_ctx* c, int s, const double* a, const double* b, const double* cs) {
-  if (!c || !a || !b || !cs || s < 1 || s > kMaxStages) return ES_ERR_INVALID;
+  if (!c) return ES_ERR_INVALID;
   Tableau t;
-  std::memset(&t, 0, sizeof(t));
-  double bsum = 0.0;
-  for (int i = 0; i < s; ++i) {
-    double row = 0.0;
-    for (int j = 0; j < s; ++j) {
-      const double v = a[i * s + j];
-      if (!std::isfinite(v) || (j >= i && v != 0.0)) return ES_ERR_INVALID;  // explicit: strictly lower
-      if (j < i) t.a[i][j] = v;
-      row += v;
-    }
-    if (!std::isfinite(b[i]) || !std::isfinite(cs[i])) return ES_ERR_INVALID;
-    // Eq. (eta-est-1-RK) bounds the entropy only for non-negative weights
-    if (c->eng.relax != ES_RELAX_NONE && b[i] < 0.0) return ES_ERR_INVALID;
-    if (std::fabs(row - cs[i]) > 1e-13 * (1.0 + std::fabs(cs[i]))) return ES_ERR_INVALID;
-    t.b[i] = b[i];
-    t.c[i] = cs[i];
-    bsum += b[i];
-  }
-  if (std::fabs(bsum - 1.0) > 1e-13) return ES_ERR_INVALID;
-  int se = s;
-  while (se > 0 && t.b[se - 1] == 0.0) --se;
-  t.s = se;
-  Group& g = c->g;
-  for (int i = g.nk; i < se; ++i) {
-    const int rc = dev_alloc_bytes(&g.k[i], 5 * g.N * g.tf);
-    if (rc != ES_OK) return rc;
-    g.nk = i + 1;
-  }
-  c->eng.tab = t;
-  return ES_OK;
+  int rc = parse_tableau(c->eng.relax, s, a, b, cs, &t);
+  if (rc == ES_OK) rc = ensure_stage_buffers(c->g, t.s);
+  if (rc == ES_OK) c->eng.tab = t;
+  return rc;
 }
 
 int es_entropy(es_ctx* c, const double* q, double* eta, void* stream) {
@@ -1225,6 +1240,23 @@ int es_batch_set_dt(es_batch* b, const double* dt_host) {
       rc = cuda_check(cudaMemcpy(g.geom_dev, g.geom.data(), g.ninst * sizeof(InstGeom), cudaMemcpyHostToDevice));
   }
   return rc;
+}
+
+int es_batch_set_tableau(es_batch* b, int s, const double* a, const double* bw, const double* cs) {
+  if (!b) return ES_ERR_INVALID;
+  Tableau t;
+  int rc = parse_tableau(b->eng.relax, s, a, bw, cs, &t);
+  if (rc != ES_OK) return rc;
+  rc = cuda_check(cudaDeviceSynchronize());  // no captured step in flight
+  for (auto& g : b->groups)
+    if (rc == ES_OK) rc = ensure_stage_buffers(g, t.s);
+  if (rc != ES_OK) return rc;
+  if (b->exec) {  // the next es_batch_advance captures the new stages
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->eng.tab = t;
+  return ES_OK;
 }
 
 int es_batch_autotune(es_batch* b, void* stream) {

@@ -241,6 +241,10 @@ class BatchSolver:
     def autotune(self, stream=None):
         B.es_batch_autotune(self.b, stream)
 
+    def set_tableau(self, A, b, c):
+        """Explicit Runge--Kutta tableau (up to 10 stages) for every instance."""
+        B.es_batch_set_tableau(self.b, A, b, c)
+
     def advance(self, nsteps, stream=None):
         B.es_batch_advance(self.b, nsteps, stream)
 

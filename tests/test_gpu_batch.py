@@ -151,15 +151,17 @@ def test_single_context_autotune_keeps_results():
     s.close()
 
 
-def test_batch_rk65_equals_single_contexts():
+@pytest.mark.parametrize("loaded", [False, True])
+def test_batch_rk65_equals_single_contexts(loaded):
     """The fifth-order RK(6,5) (rows of up to five earlier stages: the run-time stage count
-    of the stage preparation) inside the captured batch graph: bit-identical to each
-    instance alone in its own context."""
+    of the stage preparation) inside the captured batch graph, built in or loaded with
+    es_batch_set_tableau after a first captured BS3 step: bit-identical to each instance
+    alone in its own context."""
     from paper_2003_08831_gb300 import _binding as B
     from paper_2003_08831_gb300.solver import BatchSolver, Solver
     insts = instances(4, seed=31)
     nsteps = 3
-    b = BatchSolver(insts, rk=B.ES_RK_RK65)
+    b = BatchSolver(insts, rk=B.ES_RK_BS3 if loaded else B.ES_RK_RK65)
     dts = []
     for i, inst in enumerate(insts):
         mesh = dg.Mesh(inst["p"], inst["n"], inst["lo"], inst["hi"])
@@ -168,6 +170,12 @@ def test_batch_rk65_equals_single_contexts():
         b.set_state(i, q0)
         dts.append(rk.stable_dt(mesh, mesh.unflat(q0), dg.Physics(G, diss=1), 0.5))
     b.set_dt(dts)
+    if loaded:
+        b.advance(1)                      # a graph with the BS3 stages exists ...
+        for i, inst in enumerate(insts):  # ... and is replaced after the tableau changes
+            xyz = b.coords(i)
+            b.set_state(i, initial(inst, xyz[0], xyz[1]))
+        b.set_tableau(rk.RK65["A"], rk.RK65["b"], rk.RK65["c"])
     b.advance(nsteps)
     assert b.status() == 0
     for i, inst in enumerate(insts):
