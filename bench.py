@@ -319,7 +319,7 @@ def measure_device(wl, steps, warmup, dist=None, clocks_gpu=None):
 
 
 def measure_batch(precision, steps, warmup, count=256, ref_states=None, keep_states=False):
-    """Config 5 form: `count` independent isentropic-vortex instances (seeded n in 4..12,
+    """Batched form: `count` independent isentropic-vortex instances (seeded n in 4..12,
     p in 2..5, centre, strength, Mach), per-instance dt at CFL 0.5, all advanced
     together by CUDA-graph replay after the volume tiles are autotuned."""
     import torch

@@ -1,4 +1,4 @@
-"""Batched instances (config 5 form): uneven degrees and element counts in one
+"""Batched instances (256-instance vortex form): uneven degrees and element counts in one
 batch, one captured graph per step, per-instance dt / gamma / t.
 
 Checked against the FP64 oracle run instance by instance, against single-instance

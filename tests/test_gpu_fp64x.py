@@ -51,7 +51,7 @@ def test_fp64x_rhs_and_entropy_rate(p, n, mu, diss):
     s.close()
 
 
-def test_fp64x_advance_vortex_config1():
+def test_fp64x_advance_vortex_4cubed_p3():
     """4^3 elements, p = 3, [0,10]^3, BS3, CFL 0.5, 20 locally relaxed steps."""
     mesh, U, lo, hi = vortex_setup()
     g = compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=1), "BS3", 20, eps=EPS_FF, precision=_fp64x())

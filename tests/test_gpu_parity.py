@@ -177,7 +177,7 @@ def compare_advance(mesh, U, lo, hi, phys, tabname, nsteps, mode="local", cfl=0.
     return gref
 
 
-def test_advance_vortex_config1():
+def test_advance_vortex_4cubed_p3():
     """4^3 elements, p = 3, [0,10]^3, BS3, CFL 0.5, 20 steps, local relaxation (FP64)."""
     mesh, U, lo, hi = vortex_setup()
     g = compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=1), "BS3", 20)
@@ -617,7 +617,7 @@ EPS32 = 2.0 ** -23
 @pytest.mark.parametrize("prec", [1, 3])
 @pytest.mark.parametrize("p,mu,noise", [(3, 0.0, False), (4, 1.0 / 1600.0, True)])
 def test_mixed_full_size_rhs_sampled(p, mu, noise, prec):
-    """Euler TGV (config 2) and the noisy Navier--Stokes TGV (config 4) with FP32 fluxes:
+    """Euler TGV 32^3 p = 3 and the noisy Navier--Stokes TGV 32^3 p = 4 with FP32 fluxes:
     es_rhs per node within 256 eps_32 of the summed term magnitudes of the oracle."""
     mesh, U, lo, hi = tgv_full(p, noise=noise)
     phys = dg.Physics(G, mu=mu, Pr=0.72, diss=1)
