@@ -63,6 +63,12 @@ def test_fp64x_advance_rk4_ec_ragged():
     compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=0), "RK4", 6, eps=EPS_FF, precision=_fp64x())
 
 
+def test_fp64x_advance_rk65():
+    """Six stages: the float-float stage preparation with a run-time count of earlier stages."""
+    mesh, U, lo, hi = vortex_setup(N=4, p=3, nz=1)
+    compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=1), "RK65", 6, eps=EPS_FF, precision=_fp64x())
+
+
 def test_fp64x_advance_navier_stokes():
     mesh, U, lo, hi = vortex_setup(N=3, p=4, nz=2)
     compare_advance(mesh, U, lo, hi, dg.Physics(G, mu=0.005, Pr=0.72, diss=1), "BS3", 5, eps=EPS_FF,

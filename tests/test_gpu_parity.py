@@ -383,15 +383,21 @@ def test_mixed_rhs_error(p, n, mu):
 
 
 @pytest.mark.parametrize("prec", [1, 3])
-@pytest.mark.parametrize("case", ["vortex", "tgv_noise_ns"])
+@pytest.mark.parametrize("case", ["vortex", "tgv_noise_ns", "vortex_rk65"])
 def test_mixed_advance_error(case, prec):
     """Mixed-precision relaxed steps against the FP64 oracle, with FP64 (ES_MIXED) and
     float-float (ES_MIXED_FF) estimates: state relative L2 <= 1e-5."""
     from paper_2003_08831_gb300 import _binding as B
+    tab, rkc = rk.BS3, B.ES_RK_BS3
     if case == "vortex":
         mesh, U, lo, hi = vortex_setup()
         phys = dg.Physics(G, diss=1)
         nsteps = 20
+    elif case == "vortex_rk65":
+        mesh, U, lo, hi = vortex_setup()
+        phys = dg.Physics(G, diss=1)
+        nsteps = 8
+        tab, rkc = rk.RK65, B.ES_RK_RK65
     else:
         lo, hi = (0.0, 0.0, 0.0), (2 * np.pi,) * 3
         mesh = dg.Mesh(4, (4, 4, 4), lo, hi)
@@ -400,8 +406,8 @@ def test_mixed_advance_error(case, prec):
         phys = dg.Physics(G, mu=1.0 / 1600.0, Pr=0.72, diss=1)
         nsteps = 10
     dt = rk.stable_dt(mesh, U, phys, 0.5)
-    Uo, to, hist = rk.advance(mesh, U, dt, nsteps, phys, rk.BS3)
-    s = solver(mesh.p, mesh.n, lo, hi, mu=phys.mu, precision=prec)
+    Uo, to, hist = rk.advance(mesh, U, dt, nsteps, phys, tab)
+    s = solver(mesh.p, mesh.n, lo, hi, mu=phys.mu, precision=prec, rk=rkc)
     q = s.to_device(U)
     t, gh, gk = s.advance(q, nsteps, dt)
     assert s.status() == 0
