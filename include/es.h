@@ -4,8 +4,9 @@
  * Method: Ranocha, Dalcin & Parsani, "Fully-discrete explicit locally
  * entropy-stable schemes for the compressible Euler and Navier--Stokes
  * equations" (2020).  The library advances u' = f(u) (Eq. (ode)) where f is
- * the SBP-SAT semidiscretisation of Eq. (compressible_ns_diss) on a periodic
- * Cartesian mesh of LGL hexahedra, with an explicit Runge--Kutta method
+ * the SBP-SAT semidiscretisation of Eq. (compressible_ns_diss) on a Cartesian
+ * mesh of LGL hexahedra (periodic, or with the Dirichlet-penalty boundaries of
+ * es_set_boundary), with an explicit Runge--Kutta method
  * (Eq. (RK-step)) and the local relaxation of Eq. (relaxation-local-gamma)
  * with gamma = min_kappa gamma_kappa (Theorem 2.3).
  *
@@ -52,8 +53,11 @@ extern "C" {
                       entropy-variable increments, entropy sums and gamma solve */
 #define ES_FP64X 2 /* fluxes/SATs/viscous terms in float-float arithmetic on the FP32 pipe
                       (hi + lo pairs of floats, ~2^-47 relative per operation, FP32 exponent
-                      range); FP64 state, entropy sums and gamma solve.  es_rhs_noalloc
-                      evaluates such a configuration with the FP64 kernels. */
+                      range), and so are the stage states, entropy-variable increments,
+                      element sums and the gamma solve (joined to FP64 once per element);
+                      FP64 state.  Meets the FP64 parity bars with the float-float rounding
+                      unit.  es_rhs_noalloc evaluates such a configuration with the FP64
+                      kernels. */
 #define ES_MIXED_FF 3 /* FP32 fluxes/SATs/viscous terms as ES_MIXED; the stage states,
                       entropy-variable increments, the per-element sums and the gamma
                       solve in float-float on the FP32 pipe (FP64 state, FP64 gamma). */
