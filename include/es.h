@@ -105,7 +105,8 @@ void es_destroy(es_ctx* ctx);
 
 /* f(q) of Eq. (ode): dqdt[5][K][Np] = the right-hand side of
  * Eq. (compressible_ns_diss) (volume flux differencing 2 D o F 1, SAT^I
- * (+ diss^I), BR1 viscous terms and SAT^V when mu > 0).  If E_elem is not
+ * (+ diss^I), BR1 viscous terms and SAT^V when mu > 0, + diss^V when also
+ * visc_diss > 0).  If E_elem is not
  * NULL, E_elem[K] = (eta_kappa' f)(q) = sum_n P_n w(q_n).dqdt_n
  * (the integrand of Eq. (eta-est-1-RK)).  q and dqdt must not overlap. */
 int es_rhs(es_ctx* ctx, const double* q, double* dqdt, double* E_elem, void* stream);
