@@ -30,18 +30,19 @@ def test_scratch_size_limit_is_checked_on_the_host():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("p,n,mu,precision", [(3, (5, 4, 3), 0.0, 0), (4, (3, 3, 4), 0.01, 0), (3, (4, 3, 5), 0.0, 1),
-                                              (4, (3, 4, 3), 0.01, 3)])
-def test_rhs_noalloc_matches_es_rhs_on_two_calls(p, n, mu, precision):
+@pytest.mark.parametrize("p,n,mu,precision,visc", [(3, (5, 4, 3), 0.0, 0, 0.0), (4, (3, 3, 4), 0.01, 0, 0.0),
+                                                   (3, (4, 3, 5), 0.0, 1, 0.0), (4, (3, 4, 3), 0.01, 3, 0.0),
+                                                   (2, (3, 4, 3), 0.02, 0, 0.5)])
+def test_rhs_noalloc_matches_es_rhs_on_two_calls(p, n, mu, precision, visc):
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
     from paper_2003_08831_gb300.solver import Solver
     lo, hi = (0.0, 0.0, 0.0), (2 * np.pi,) * 3
-    s = Solver(p, n, lo, hi, mu=mu, precision=precision)
+    s = Solver(p, n, lo, hi, mu=mu, precision=precision, visc_diss=visc)
     xyz = s.coords()
-    cfg = B.make_config(p, n, lo, hi, mu=mu, precision=precision)
+    cfg = B.make_config(p, n, lo, hi, mu=mu, precision=precision, visc_diss=visc)
     rng = np.random.default_rng(p)
     for call in range(2):   # two calls in a row: the shared scratch keeps the last contents
         q0 = inputs.tgv_state(xyz[0] + 0.3 * call, xyz[1], xyz[2], mach=0.3)
