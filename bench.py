@@ -110,7 +110,7 @@ def kernel_flops(p, n_el, stages=3):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_volume launch of the
 # default workload, from the ncu capture summarised in profiles/ (stage 3 of a step, FP64).
 # It is reported only while the kernel sources hash to the value the capture was taken with.
-VOLUME_TRAFFIC = {"source_sha1": "3d87c7d28eb6720adf6e80c37d4cbfad7583acd2", "bytes_per_launch": 399743488 + 68273408}
+VOLUME_TRAFFIC = {"source_sha1": "de78239ba2e03a5495b6bae9234e18825dfd8dc8", "bytes_per_launch": 399555840 + 67871232}
 
 
 def kernel_source_sha1():

@@ -672,27 +672,34 @@ __global__ void __launch_bounds__(THREADS) k_grad(Params P, const TF* __restrict
 #pragma unroll
       for (int c = 0; c < 4; ++c) th[m][c] = met * acc[c];
     }
-    // chain rule: v = -w_{2..4}/w_5 = z_{2..4}/z1, T = -1/(R w_5)
+    // chain rule: v = -w_{2..4}/w_5 = z_{2..4}/z1, T = -1/(R w_5).  With a = -1/w_5 = 1/z1^2
+    // and b_mk = theta_m,k + v_k theta_m,5: dv_k/dx_m = a b_mk, dT/dx_m = a^2/R theta_m,5;
+    // tau is symmetric: off-diagonal mu a (b_mk + b_km), diagonal 2 mu a b_mm - (2/3) mu a sum b_jj
     const TF iz1 = aux[5 * N + g];
     const TF v[3] = {aux[N + g] * iz1, aux[2 * N + g] * iz1, aux[3 * N + g] * iz1};
-    const TF iw5 = -iz1 * iz1;  // 1/w_5
-    TF gv[3][3], gT[3];
+    const TF a = iz1 * iz1;
+    TF b[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) b[m][k] = th[m][k] + v[k] * th[m][3];
+    const TF ma = mu * a;
+    const TF dsum = (ma * TF(-2.0 / 3.0)) * (b[0][0] + b[1][1] + b[2][2]);
+    const TF c1 = ma + ma;
+    TF tau[3][3];
+    tau[0][1] = tau[1][0] = ma * (b[0][1] + b[1][0]);
+    tau[0][2] = tau[2][0] = ma * (b[0][2] + b[2][0]);
+    tau[1][2] = tau[2][1] = ma * (b[1][2] + b[2][1]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) tau[m][m] = c1 * b[m][m] + dsum;
+    const TF kt = kap * a * a * iR;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) gv[m][k] = -(th[m][k] + v[k] * th[m][3]) * iw5;
-      gT[m] = th[m][3] * iw5 * iw5 * iR;
-    }
-    const TF divv = gv[0][0] + gv[1][1] + gv[2][2];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      TF fe = kap * gT[m];
+      TF fe = kt * th[m][3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        TF tau = mu * (gv[m][k] + gv[k][m]);
-        if (k == m) tau -= mu * TF(2.0 / 3.0) * divv;
-        fV[(long long)(m * 4 + k) * N + g] = tau;
-        fe += tau * v[k];
+        fV[(long long)(m * 4 + k) * N + g] = tau[m][k];
+        fe += tau[m][k] * v[k];
       }
       fV[(long long)(m * 4 + 3) * N + g] = fe;
     }
