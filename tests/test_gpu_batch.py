@@ -188,3 +188,40 @@ def test_batch_rk65_equals_single_contexts(loaded):
         s.close()
     b.close()
 
+
+
+def test_full_size_256_instance_batch_sampled():
+    """The 256-instance batched vortex workload as the benchmark builds it (seeded
+    instances, autotuned tiles, 23 graph-replayed steps): the smallest instance of each
+    degree against the oracle run on its own, state 1e-12 per variable and t_gamma 1e-12."""
+    from paper_2003_08831_gb300 import _binding as B
+    from paper_2003_08831_gb300.solver import BatchSolver, stable_dt
+    params = inputs.batch_instances(256)
+    insts = [dict(p=d["p"], n=(d["n"],) * 3, lo=(0.0, 0.0, 0.0), hi=(d["box"],) * 3) for d in params]
+    b = BatchSolver(insts)
+    dts, q0s = [], []
+    for i, d in enumerate(params):
+        xyz = b.coords(i)
+        q0 = inputs.vortex_state(xyz[0], xyz[1], 0.0, eps=d["eps"], mach=d["mach"], centre=d["centre"],
+                                 period=d["box"])
+        b.set_state(i, q0)
+        q0s.append(q0)
+        dts.append(stable_dt(q0, d["p"], [d["box"] / d["n"]] * 3, 0.5))
+    b.set_dt(dts)
+    b.autotune()
+    nsteps = 23
+    b.advance(nsteps)
+    assert b.status() in (0, B.ES_ERR_NO_ROOT)
+    t_gpu, _ = b.times()
+    sample = [min((i for i in range(len(params)) if params[i]["p"] == p), key=lambda i: params[i]["n"])
+              for p in (2, 3, 4, 5)]
+    for i in sample:
+        d = params[i]
+        mesh = dg.Mesh(d["p"], (d["n"],) * 3, (0.0, 0.0, 0.0), (d["box"],) * 3)
+        Uo, t, hist = rk.advance(mesh, mesh.unflat(q0s[i]), dts[i], nsteps, dg.Physics(G, diss=1), rk.BS3)
+        ref = Uo.reshape(5, -1)
+        scale = np.maximum(np.max(np.abs(ref), axis=1), 1e-3 * np.max(np.abs(ref)))
+        err = np.max(np.abs(b.get_state(i).reshape(5, -1) - ref), axis=1) / scale
+        assert np.all(err < TOL), (i, d, err)
+        assert abs(t_gpu[i] - t) < TOL * t, (i, t_gpu[i], t)
+    b.close()
