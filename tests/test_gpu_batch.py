@@ -190,15 +190,20 @@ def test_batch_rk65_equals_single_contexts(loaded):
 
 
 
-def test_full_size_256_instance_batch_sampled():
+@pytest.mark.parametrize("precision", [0, 1, 3])
+def test_full_size_256_instance_batch_sampled(precision):
     """The 256-instance batched vortex workload as the benchmark builds it (seeded
     instances, autotuned tiles, 23 graph-replayed steps): the smallest instance of each
-    degree against the oracle run on its own, state 1e-12 per variable and t_gamma 1e-12."""
+    degree against the oracle run on its own.  FP64: state 1e-12 per variable and t_gamma
+    1e-12.  FP32 fluxes (both mixed modes, the oracle with their delta_floor 4e-6): state
+    1e-5 relative (L2); t_gamma within 1e-5 or 8x its response to FP32-level changes of the
+    oracle's right-hand sides (gamma_kappa is the root of a second-order quantity; on the
+    under-resolved strong vortices gamma ~ 0.995 and it moves by ~1e-5)."""
     from paper_2003_08831_gb300 import _binding as B
     from paper_2003_08831_gb300.solver import BatchSolver, stable_dt
     params = inputs.batch_instances(256)
     insts = [dict(p=d["p"], n=(d["n"],) * 3, lo=(0.0, 0.0, 0.0), hi=(d["box"],) * 3) for d in params]
-    b = BatchSolver(insts)
+    b = BatchSolver(insts, precision=precision)
     dts, q0s = [], []
     for i, d in enumerate(params):
         xyz = b.coords(i)
@@ -218,10 +223,27 @@ def test_full_size_256_instance_batch_sampled():
     for i in sample:
         d = params[i]
         mesh = dg.Mesh(d["p"], (d["n"],) * 3, (0.0, 0.0, 0.0), (d["box"],) * 3)
-        Uo, t, hist = rk.advance(mesh, mesh.unflat(q0s[i]), dts[i], nsteps, dg.Physics(G, diss=1), rk.BS3)
+        phys = dg.Physics(G, diss=1)
+        floor = 1e-8 if precision == 0 else 4e-6
+        U0 = mesh.unflat(q0s[i])
+        Uo, t, hist = rk.advance(mesh, U0, dts[i], nsteps, phys, rk.BS3, delta_floor=floor)
         ref = Uo.reshape(5, -1)
-        scale = np.maximum(np.max(np.abs(ref), axis=1), 1e-3 * np.max(np.abs(ref)))
-        err = np.max(np.abs(b.get_state(i).reshape(5, -1) - ref), axis=1) / scale
-        assert np.all(err < TOL), (i, d, err)
-        assert abs(t_gpu[i] - t) < TOL * t, (i, t_gpu[i], t)
+        got = b.get_state(i).reshape(5, -1)
+        if precision == 0:
+            scale = np.maximum(np.max(np.abs(ref), axis=1), 1e-3 * np.max(np.abs(ref)))
+            err = np.max(np.abs(got - ref), axis=1) / scale
+            tol = TOL
+            assert abs(t_gpu[i] - t) < TOL * t, (i, t_gpu[i], t)
+        else:
+            nref = np.sqrt(np.sum(ref ** 2, axis=1))
+            err = np.sqrt(np.sum((got - ref) ** 2, axis=1)) / np.maximum(nref, 1e-3 * nref.max())
+            tol = 1e-5
+            rng = np.random.default_rng(7)
+
+            def noisy(m_, U_, p_, t=0.0):
+                R = dg.rhs(m_, U_, p_, t)
+                return R + 2 * 2.0 ** -23 * dg.rhs_term_magnitude(m_, U_, p_, t) * rng.standard_normal(R.shape)
+            _, t_n, _ = rk.advance(mesh, U0, dts[i], nsteps, phys, rk.BS3, delta_floor=floor, rhs=noisy)
+            assert abs(t_gpu[i] - t) < max(1e-5, 8 * abs(t_n - t) / t) * t, (i, t_gpu[i], t, t_n)
+        assert np.all(err < tol), (i, d, err)
     b.close()
