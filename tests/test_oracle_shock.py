@@ -80,10 +80,10 @@ def test_dirichlet_boundary_preserves_uniform_flow():
 
     def bc(t):
         return q0
-    for p, mu in [(2, 0.0), (3, 0.05)]:
+    for p, mu, diss, visc in [(2, 0.0, 1, 0.0), (3, 0.05, 1, 0.0), (3, 0.05, 2, 1.0)]:
         mesh = dg.Mesh(p, (4, 2, 3), (0, 0, 0), (1.0, 0.5, 0.75), bc={0: (bc, bc)})
         U = np.broadcast_to(q0.reshape(5, 1, 1, 1, 1, 1, 1), mesh.shape).copy()
-        R = dg.rhs(mesh, U, dg.Physics(G, mu=mu, diss=1), t=0.3)
+        R = dg.rhs(mesh, U, dg.Physics(G, mu=mu, diss=diss, visc_diss=visc), t=0.3)
         assert np.max(np.abs(R)) < 1e-13
 
 
