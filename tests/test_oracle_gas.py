@@ -123,6 +123,31 @@ def test_rusanov_dissipates_entropy():
         assert np.all(np.sum(dw * (f_es - f_ec), axis=0) <= 1e-14)
 
 
+def test_sound_speed_closed_form():
+    """c = sqrt(gamma p / rho): rho = 1, p = 1 gives sqrt(1.4); rho = 2, p = 3 gives sqrt(2.1)."""
+    q = gas.conserved(np.array([1.0, 2.0]), np.array([[0.5, -1.0], [-0.2, 0.3], [0.1, 0.0]]),
+                      np.array([1.0, 3.0]), G)
+    assert np.allclose(gas.sound_speed(q, G), [np.sqrt(1.4), np.sqrt(2.1)], rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("m,lam", [(0, 1.0 + np.sqrt(2.1)),          # right side: |-1.0| + sqrt(2.1)
+                                   (1, 0.3 + np.sqrt(2.1)),          # right side: |0.3| + sqrt(2.1)
+                                   (2, 0.4 + np.sqrt(1.4))])         # left side: |0.4| + sqrt(1.4) > sqrt(2.1)
+def test_rusanov_lambda_closed_form(m, lam):
+    """Rusanov term of the interface flux: f_num = f_ec - (lambda/2)(qR - qL) with
+    lambda = max(|vL.n| + cL, |vR.n| + cR) along the face normal e_m, for the two states
+    rho = 1, v = (0.5, -0.2, 0.4), p = 1 (c = sqrt(1.4)) and rho = 2, v = (-1, 0.3, 0),
+    p = 3 (c = sqrt(2.1)); in x3 the left side gives the larger speed.  A wrong factor on
+    c, a wrong velocity component or a min in place of the max changes lambda."""
+    qL = gas.conserved(np.array(1.0), np.array([0.5, -0.2, 0.4]), np.array(1.0), G)
+    qR = gas.conserved(np.array(2.0), np.array([-1.0, 0.3, 0.0]), np.array(3.0), G)
+    f_ec = gas.interface_flux(qL, qR, G, m, 0)
+    f_rus = gas.interface_flux(qL, qR, G, m, 1)
+    jump = qR - qL
+    assert np.all(np.abs(jump) > 0.05)
+    assert np.allclose((f_ec - f_rus) / (0.5 * jump), lam, rtol=1e-13, atol=0)
+
+
 def _jacobian(fun, x, h=1e-6):
     """Central-difference Jacobian of a vector function of a 5-vector."""
     J = np.empty((5, 5))
