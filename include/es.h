@@ -227,7 +227,12 @@ int es_profile_read(es_ctx* ctx, double* ms, long long* launches);
  * make that first call before any stream capture.  All calls share the array
  * and the status word inside it, so calls that overlap on the GPU (different
  * streams, or different host threads) race: serialise them.  Device-side
- * errors (non-physical states) are not reported by this call. */
+ * errors (non-physical states) are not reported by this call.
+ * CUDA errors: if the calling thread already has a pending CUDA error from
+ * earlier work, the call returns ES_ERR_CUDA before enqueueing anything and
+ * leaves that error pending (it stays the caller's to read).  A runtime call or
+ * launch of this entry point that fails returns ES_ERR_CUDA and clears the
+ * error it raised, so it is not reported again by a later call. */
 #define ES_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqdt, double* E_elem, void* stream);
 /* Scratch bytes es_rhs_noalloc needs for cfg (0 if cfg is invalid). */

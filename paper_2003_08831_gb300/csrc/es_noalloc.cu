@@ -40,23 +40,34 @@ int dispatch_p1(int P1, bool fp64, F&& f) {
   return ES_ERR_INVALID;
 }
 
+// A runtime call that failed also left its error as the thread's last error; it is
+// taken back here so that the next call (ours or the caller's) does not report it.
+int failed(cudaError_t e, const char* what) {
+  std::fprintf(stderr, "es_rhs_noalloc: %s failed: %s\n", what, cudaGetErrorString(e));
+  cudaGetLastError();
+  return ES_ERR_CUDA;
+}
+
 int setup_device(int dev) {
   if (g_ready[dev]) return ES_OK;
   void* ptr = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-  if (e != cudaSuccess) {
-    std::fprintf(stderr, "es_rhs_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
-    return ES_ERR_CUDA;
-  }
+  if (e != cudaSuccess) return failed(e, "cudaGetSymbolAddress");
   int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ES_ERR_CUDA;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return failed(e, "cudaDeviceGetAttribute");
   // opt the volume kernels into their dynamic shared memory (no allocation)
   for (int P1 = 3; P1 <= 6; ++P1) {
     for (int fp64 = 0; fp64 < 2; ++fp64) {
-      const int rc = dispatch_p1(P1, fp64 != 0, [](auto L) {
-        return decltype(L)::volume_setup() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
-      });
-      if (rc != ES_OK) return rc;
+      const cudaError_t es = [&] {
+        cudaError_t r = cudaSuccess;
+        dispatch_p1(P1, fp64 != 0, [&](auto L) {
+          r = decltype(L)::volume_setup();
+          return ES_OK;
+        });
+        return r;
+      }();
+      if (es != cudaSuccess) return failed(es, "cudaFuncSetAttribute");
     }
   }
   g_scratch_ptr[dev] = ptr;
@@ -85,11 +96,14 @@ extern "C" int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqd
   if (validate_config(*cfg) != ES_OK) return ES_ERR_INVALID;
   const size_t need = es_rhs_noalloc_scratch_bytes(cfg);
   if (need > kNoallocScratchBytes) return ES_ERR_TOO_LARGE;
+  // an error left pending by earlier work stays the caller's: it is reported here
+  // (before anything is enqueued) and not cleared, so that the launch check at the
+  // end sees only this call's launches
+  if (cudaPeekAtLastError() != cudaSuccess) return ES_ERR_CUDA;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return ES_ERR_CUDA;
-  }
+  cudaError_t de = cudaGetDevice(&dev);
+  if (de != cudaSuccess) return failed(de, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return ES_ERR_CUDA;
   int rc = setup_device(dev);
   if (rc != ES_OK) return rc;
 
@@ -112,7 +126,8 @@ extern "C" int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqd
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // the status word accumulates bits with atomicOr: it must start at zero
-  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return ES_ERR_CUDA;
+  const cudaError_t me = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (me != cudaSuccess) return failed(me, "cudaMemsetAsync");
   StagePrep sp = {};
   sp.q = const_cast<double*>(q);  // read only: apply_update = 0
   sp.Np = int(Np);
@@ -127,7 +142,10 @@ extern "C" int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqd
     Lc::face(P, aux, F, nullptr, st, grid_for_sms(sms, 3LL * K * P1 * P1, 256));
     if (ns) Lc::grad(P, aux, fV, st, grid_for_sms(sms, N, 256));
     Lc::volume(P, sv, aux, F, nullptr, fV, ns, st, 0);
-    return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
+    return ES_OK;
   });
-  return rc;
+  if (rc != ES_OK) return rc;
+  // the launches' own errors (no earlier error was pending at entry)
+  const cudaError_t le = cudaGetLastError();
+  return le == cudaSuccess ? ES_OK : failed(le, "kernel launch");
 }

@@ -19,6 +19,8 @@ TOL = 1e-12
 
 def test_scratch_size_limit_is_checked_on_the_host():
     """Sizes beyond the fixed scratch are rejected before any GPU work (no GPU needed)."""
+    import __graft_entry__
+    __graft_entry__.build()
     lib = B.load()
     small = B.make_config(3, (4, 4, 4))
     big = B.make_config(5, (40, 40, 40), mu=0.01)
@@ -32,15 +34,19 @@ def test_scratch_size_limit_is_checked_on_the_host():
 @pytest.mark.gpu
 @pytest.mark.parametrize("p,n,mu,precision,visc", [(3, (5, 4, 3), 0.0, 0, 0.0), (4, (3, 3, 4), 0.01, 0, 0.0),
                                                    (3, (4, 3, 5), 0.0, 1, 0.0), (4, (3, 4, 3), 0.01, 3, 0.0),
-                                                   (2, (3, 4, 3), 0.02, 0, 0.5)])
+                                                   (2, (3, 4, 3), 0.02, 0, 0.5), (3, (4, 5, 3), 0.01, 2, 0.0)])
 def test_rhs_noalloc_matches_es_rhs_on_two_calls(p, n, mu, precision, visc):
+    """An ES_FP64X config (precision 2) runs on the FP64 kernels here, so its reference is
+    es_rhs of an ES_FP64 context on the same mesh; the other modes compare with es_rhs of
+    a context of the same precision."""
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
     from paper_2003_08831_gb300.solver import Solver
     lo, hi = (0.0, 0.0, 0.0), (2 * np.pi,) * 3
-    s = Solver(p, n, lo, hi, mu=mu, precision=precision, visc_diss=visc)
+    ref_precision = B.ES_FP64 if precision == B.ES_FP64X else precision
+    s = Solver(p, n, lo, hi, mu=mu, precision=ref_precision, visc_diss=visc)
     xyz = s.coords()
     cfg = B.make_config(p, n, lo, hi, mu=mu, precision=precision, visc_diss=visc)
     rng = np.random.default_rng(p)
