@@ -93,6 +93,13 @@ typedef struct {
                            alpha (2/h_m)(1/omega_0) (C_mm(q-) + C_mm(q+))/2 (w- - w+)
                            added to the interface flux, C_mm the viscous-flux block
                            of dw/dx_m (symmetric positive semidefinite) */
+  double root_rtol;     /* stop of the gamma_kappa root solve (Section 4 leaves the
+                           solver open): a Newton step |s| <= root_rtol gamma ends it
+                           (the updated iterate is returned), as does a bracket of
+                           width <= 4 2^-52 max(1, gamma).  In [0, 1); 0 selects 1e-8,
+                           whose quadratic convergence leaves an error near 1e-16 gamma.
+                           The float-float solves (ES_FP64X, ES_MIXED_FF) use at least
+                           2^-40 and stop at a bracket of width 2^-44 max(1, gamma). */
 } es_config;
 
 /* Mesh, LGL/SBP tables (Section 3.1: diagonal-norm SBP on LGL nodes) and
@@ -173,6 +180,24 @@ int es_relax_step(es_ctx* ctx, const double* u_old, const double* u_new, const d
 int es_advance(es_ctx* ctx, double* q, int nsteps, double dt, double* t, double* gamma_hist,
                double* gamma_elem, void* stream);
 
+/* One relaxed step (es_advance with nsteps = 1) that also returns both sides of
+ * the local entropy inequality of Theorem 2.3,
+ *   eta_kappa(u^n) <= eta_kappa(u^{n-1}) + gamma (eta_kappa^new - eta_kappa(u^{n-1})),
+ * per element, all device arrays of K doubles (any may be NULL):
+ *   eta_old[e]  = eta_kappa(u^{n-1}) = sum_n P_n S(u_n) (as es_entropy computes it);
+ *   deta[e]     = eta_kappa^new - eta_kappa(u^{n-1}) = dt sum_i b_i (eta_kappa' f)(y^i),
+ *                 the estimate of Eq. (eta-est-1-RK) formed from the step's own stage
+ *                 values (those the relaxation used: FP32 right-hand sides in the
+ *                 mixed modes) as sum_n P_n w(u_n).d_n - A_kappa in FP64;
+ *   eta_new[e]  = eta_kappa(u^n) after the relaxed update (es_entropy of q);
+ *   gamma_elem  = the step's gamma_kappa (+inf where unconstrained), *gamma (device
+ *                 scalar) the step's gamma.
+ * q (device, in place) and *t (device, may be NULL) advance as in es_advance.  With
+ * ES_RELAX_NONE the estimate is still formed (gamma = 1), so the baseline step's
+ * inequality can be checked too. */
+int es_step_estimate(es_ctx* ctx, double* q, double dt, double* t, double* gamma, double* gamma_elem,
+                     double* eta_old, double* deta, double* eta_new, void* stream);
+
 /* es_advance on HOST buffers: copies q_host (5 K Np doubles) and *t_host to
  * the context's device buffers, advances, and copies q, t and gamma_hist
  * (nsteps doubles, may be NULL) back; returns after the stream completes.
@@ -238,10 +263,21 @@ int es_rhs_noalloc(const es_config* cfg, const double* q, double* dqdt, double* 
 /* Scratch bytes es_rhs_noalloc needs for cfg (0 if cfg is invalid). */
 size_t es_rhs_noalloc_scratch_bytes(const es_config* cfg);
 
-/* Volume-kernel tile autotuning for this context: times every tile variant
- * (elements per CTA x threads) of the flux-differencing kernel on the state q
- * (device, [5][K][Np]) and keeps the fastest for later calls.  Synchronises. */
+/* Volume-kernel tile autotuning for this context: times every usable variant
+ * (es_volume_variant) on two stages of the state q (device, [5][K][Np]; q is not
+ * changed) and keeps the fastest for later calls.  Synchronises. */
 int es_autotune(es_ctx* ctx, const double* q, void* stream);
+
+/* The tile variant in use: 0..2 run the stage as k_prep + k_face + k_volume with one
+ * of three (elements per CTA x threads) tiles of the flux-differencing kernel; 3..5
+ * run the same tiles as one fused kernel per stage (available for FP32 fluxes,
+ * ES_MIXED and ES_MIXED_FF, on periodic Euler meshes, where it is the default), which
+ * forms the parameter vector and the interface fluxes on chip instead of storing them.
+ * Every variant gives bit-identical results.  es_set_volume_variant returns
+ * ES_ERR_INVALID for a variant outside 0..5 or a fused one the context cannot use;
+ * es_autotune picks among all usable variants. */
+int es_volume_variant(const es_ctx* ctx);
+int es_set_volume_variant(es_ctx* ctx, int variant);
 
 /* ---- Batches: many independent instances advanced together -------------
  * Instances may differ in LGL degree and element counts (and box) but share
@@ -274,6 +310,16 @@ int es_batch_volume_variant(const es_batch* b, int inst);
 /* nsteps relaxed steps of every instance (graph replay), ordered after prior
  * work on `stream`; later work on `stream` waits for it */
 int es_batch_advance(es_batch* b, int nsteps, void* stream);
+/* es_step_estimate for every instance of the batch: one relaxed step of all
+ * instances (the same kernels as es_batch_advance, launched on `stream` instead of
+ * replaying the graph) that keeps each element's eta_kappa(u^{n-1}), estimate
+ * deta_kappa and eta_kappa(u^n) in the batch (allocated on the first call,
+ * ES_ERR_NOMEM).  es_batch_get_estimate copies instance inst's values and its last
+ * gamma_kappa to host arrays of K_i doubles (any may be NULL; synchronises;
+ * ES_ERR_INVALID before the first es_batch_step_estimate). */
+int es_batch_step_estimate(es_batch* b, void* stream);
+int es_batch_get_estimate(es_batch* b, int inst, double* eta_old_host, double* deta_host, double* eta_new_host,
+                          double* gamma_elem_host);
 /* per-instance t and last gamma (host arrays of count, either may be NULL); synchronises */
 int es_batch_times(es_batch* b, double* t_host, double* gamma_host);
 int es_batch_status(es_batch* b, void* stream);
@@ -286,6 +332,14 @@ long long es_batch_launch_count(const es_batch* b);
  * flux, thermodynamics and relaxation kernels in place of IEEE division.
  * Exposed so that it can be checked against IEEE division; x must be normal. */
 int es_reciprocal(const double* x, double* out, long long n, void* stream);
+
+/* ALU throughput of this GPU (instrumentation, not part of the method): *tflops =
+ * the rate at which independent fused multiply-adds retire on every SM, FP64 if fp64
+ * is nonzero, else FP32 (2 flops per FMA; eight independent chains per thread, 64
+ * warps per SM, one warm-up launch, five launches timed with CUDA events on
+ * `stream`).  It is the measured denominator of the roofline of the ALU-bound
+ * kernels.  Allocates and frees a small output buffer; synchronises `stream`. */
+int es_fma_peak(int fp64, double* tflops, void* stream);
 
 /* Static message for an ES_* code. */
 const char* es_strerror(int code);

@@ -30,7 +30,8 @@ EXPORTS = ["es_create", "es_destroy", "es_rhs", "es_entropy", "es_relax_step", "
            "es_batch_set_state", "es_batch_get_state", "es_batch_set_dt", "es_batch_autotune",
            "es_batch_volume_variant", "es_batch_advance", "es_batch_times", "es_batch_status",
            "es_batch_launch_count", "es_reciprocal", "es_set_boundary", "es_set_time", "es_set_tableau",
-           "es_batch_set_tableau"]
+           "es_batch_set_tableau", "es_step_estimate", "es_batch_step_estimate", "es_batch_get_estimate", "es_fma_peak", "es_volume_variant",
+           "es_set_volume_variant"]
 KERNEL_KINDS = ["prep", "face", "grad", "volume", "relax", "other"]
 
 
@@ -40,7 +41,7 @@ class es_config(ctypes.Structure):
                 ("gamma_gas", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("R", ctypes.c_double), ("interface_diss", ctypes.c_int), ("relax", ctypes.c_int),
                 ("rk", ctypes.c_int), ("precision", ctypes.c_int), ("delta_floor", ctypes.c_double),
-                ("visc_diss", ctypes.c_double)]
+                ("visc_diss", ctypes.c_double), ("root_rtol", ctypes.c_double)]
 
 
 class ESError(RuntimeError):
@@ -128,6 +129,18 @@ def load(path=None):
     lib.es_set_tableau.restype = i
     lib.es_batch_set_tableau.argtypes = [vp, i, vp, vp, vp]
     lib.es_batch_set_tableau.restype = i
+    lib.es_step_estimate.argtypes = [vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
+    lib.es_step_estimate.restype = i
+    lib.es_batch_step_estimate.argtypes = [vp, vp]
+    lib.es_batch_step_estimate.restype = i
+    lib.es_batch_get_estimate.argtypes = [vp, i, vp, vp, vp, vp]
+    lib.es_batch_get_estimate.restype = i
+    lib.es_volume_variant.argtypes = [vp]
+    lib.es_volume_variant.restype = i
+    lib.es_set_volume_variant.argtypes = [vp, i]
+    lib.es_set_volume_variant.restype = i
+    lib.es_fma_peak.argtypes = [i, vp, vp]
+    lib.es_fma_peak.restype = i
     lib.es_strerror.argtypes = [i]
     lib.es_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -172,7 +185,7 @@ def _stream(stream):
 
 def make_config(p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0,
                 interface_diss=1, relax=ES_RELAX_LOCAL, rk=ES_RK_BS3, precision=ES_FP64, delta_floor=0.0,
-                visc_diss=0.0):
+                visc_diss=0.0, root_rtol=0.0):
     c = es_config()
     c.p = p
     c.nx, c.ny, c.nz = n
@@ -182,6 +195,7 @@ def make_config(p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma_gas=1.4, mu=
     c.interface_diss, c.relax, c.rk, c.precision = interface_diss, relax, rk, precision
     c.delta_floor = delta_floor
     c.visc_diss = visc_diss
+    c.root_rtol = root_rtol
     return c
 
 
@@ -250,6 +264,12 @@ def es_advance(ctx, q, nsteps, dt, t, gamma_hist=None, gamma_elem=None, stream=N
                              _stream(stream)), "es_advance")
 
 
+def es_step_estimate(ctx, q, dt, t=None, gamma=None, gamma_elem=None, eta_old=None, deta=None, eta_new=None,
+                     stream=None):
+    _check(load().es_step_estimate(ctx, _ptr(q), float(dt), _ptr(t), _ptr(gamma), _ptr(gamma_elem), _ptr(eta_old),
+                                   _ptr(deta), _ptr(eta_new), _stream(stream)), "es_step_estimate")
+
+
 def es_advance_host(ctx, q_host, nsteps, dt, t_host, gamma_hist_host=None, stream=None):
     _check(load().es_advance_host(ctx, _ptr(q_host), int(nsteps), float(dt), _ptr(t_host), _ptr(gamma_hist_host),
                                   _stream(stream)), "es_advance_host")
@@ -292,6 +312,14 @@ def es_rhs_noalloc(cfg, q, dqdt, E_elem=None, stream=None):
 
 def es_rhs_noalloc_scratch_bytes(cfg):
     return int(load().es_rhs_noalloc_scratch_bytes(ctypes.byref(cfg)))
+
+
+def es_volume_variant(ctx):
+    return int(load().es_volume_variant(ctx))
+
+
+def es_set_volume_variant(ctx, variant):
+    _check(load().es_set_volume_variant(ctx, int(variant)), "es_set_volume_variant")
 
 
 def es_autotune(ctx, q, stream=None):
@@ -343,6 +371,15 @@ def es_batch_advance(b, nsteps, stream=None):
     _check(load().es_batch_advance(b, int(nsteps), _stream(stream)), "es_batch_advance")
 
 
+def es_batch_step_estimate(b, stream=None):
+    _check(load().es_batch_step_estimate(b, _stream(stream)), "es_batch_step_estimate")
+
+
+def es_batch_get_estimate(b, inst, eta_old_host=None, deta_host=None, eta_new_host=None, gamma_elem_host=None):
+    _check(load().es_batch_get_estimate(b, int(inst), _ptr(eta_old_host), _ptr(deta_host), _ptr(eta_new_host),
+                                        _ptr(gamma_elem_host)), "es_batch_get_estimate")
+
+
 def es_batch_times(b, t_host=None, gamma_host=None):
     _check(load().es_batch_times(b, _ptr(t_host), _ptr(gamma_host)), "es_batch_times")
 
@@ -353,6 +390,13 @@ def es_batch_status(b, stream=None):
 
 def es_batch_launch_count(b):
     return int(load().es_batch_launch_count(b))
+
+
+def es_fma_peak(fp64, stream=None):
+    """Measured FMA throughput of the current GPU in TFLOP/s (FP64 if fp64 else FP32)."""
+    out = ctypes.c_double(0.0)
+    _check(load().es_fma_peak(int(bool(fp64)), ctypes.byref(out), _stream(stream)), "es_fma_peak")
+    return out.value
 
 
 def es_reciprocal(x, out, stream=None):

@@ -15,7 +15,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libes.so")
 
-SOURCES = ["es_api.cu", "es_noalloc.cu", "es_kernels_p3.cu", "es_kernels_p4.cu", "es_kernels_p5.cu", "es_kernels_p6.cu",
+SOURCES = ["es_api.cu", "es_noalloc.cu", "es_peak.cu", "es_kernels_p3.cu", "es_kernels_p4.cu", "es_kernels_p5.cu", "es_kernels_p6.cu",
            "es_kernels_ff_p3.cu", "es_kernels_ff_p4.cu", "es_kernels_ff_p5.cu", "es_kernels_ff_p6.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

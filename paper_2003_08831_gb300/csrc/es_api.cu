@@ -151,6 +151,7 @@ int validate_config(const es_config& C) {
   if (!(C.visc_diss >= 0.0) || !std::isfinite(C.visc_diss)) return ES_ERR_INVALID;
   if (C.relax != ES_RELAX_NONE && C.relax != ES_RELAX_LOCAL && C.relax != ES_RELAX_GLOBAL) return ES_ERR_INVALID;
   if (C.interface_diss < 0 || C.interface_diss > 2) return ES_ERR_INVALID;
+  if (!(C.root_rtol >= 0.0) || !(C.root_rtol < 1.0)) return ES_ERR_INVALID;
   for (int m = 0; m < 3; ++m)
     if (!(C.hi[m] > C.lo[m])) return ES_ERR_INVALID;
   const long long K = (long long)C.nx * C.ny * C.nz;
@@ -273,7 +274,12 @@ struct Group {
   bool any_bc = false;
   void* FL = nullptr;                    // -x_m boundary-face fluxes (tf bytes each)
   double* bcz = nullptr;                 // [3][2][kBcVals] exterior values at the stage time
+  double* est = nullptr;                 // batch estimate step: eta_old, deta, eta_new [3][K]
 };
+
+// The fused stage kernel serves FP32 fluxes (ES_MIXED, ES_MIXED_FF) on periodic Euler groups.
+bool stage_fusable(const Group& g) { return g.tf == 4 && g.cfg.mu == 0.0 && !g.any_bc; }
+bool stage_fused(const Group& g) { return g.vol_variant >= kVolumeVariants && stage_fusable(g); }
 
 // Launch bookkeeping shared by a context or a batch.
 struct Engine {
@@ -448,6 +454,7 @@ void group_free(Group& g) {
   cudaFree(g.elem_inst_dev);
   cudaFree(g.FL);
   cudaFree(g.bcz);
+  cudaFree(g.est);
   g = Group();
 }
 
@@ -556,6 +563,8 @@ int group_init(Group& g, const es_config* insts, int n, int stages, bool own_sta
     rc = cuda_check(cudaDeviceSynchronize());
   }
   if (rc == ES_OK) rc = dispatch(g, [&](auto L) { return cuda_check(decltype(L)::volume_setup()); });
+  if (rc == ES_OK) rc = dispatch(g, [&](auto L) { return cuda_check(decltype(L)::stage_setup()); });
+  if (stage_fusable(g)) g.vol_variant = kVolumeVariants;  // fused, default tile
   return rc;
 }
 
@@ -618,10 +627,25 @@ void launch_bc_eval(const BcSpec& spec, const double* t, double t_off, double* o
 int grid_for(const Engine& e, long long n, int block) { return grid_for_sms(e.sm_count, n, block); }
 
 // One stage's right-hand side into kout or d (+ element sums), on state u (+ pending
-// update) + dt sum_j coef[j] k[j].
+// update) + dt sum_j coef[j] k[j].  With a fused variant (stage_fused) one k_stage launch
+// replaces k_prep, k_face and k_volume; it forms the entropy-variable increments itself
+// (sp.dw / sv.dw only say that this stage needs them) and cannot apply a pending update.
 int run_stage(Engine& E, Group& g, const StagePrep& sp, const StageVol& sv, cudaStream_t st,
               const double* t_dev = nullptr, double t_off = 0.0) {
   const bool ns = g.cfg.mu != 0.0;
+  if (stage_fused(g)) {
+    if (sp.pending) return ES_ERR_INVALID;
+    StagePrep sp2 = sp;
+    sp2.dw = nullptr;
+    StageVol sv2 = sv;
+    sv2.dw_inline = sv.dw != nullptr;
+    sv2.dw = nullptr;
+    return dispatch(g, [&](auto L) {
+      timed(E, ES_KERNEL_VOLUME, st,
+            [&] { decltype(L)::stage(g.P, sp2, sv2, E.status, st, g.vol_variant - kVolumeVariants); });
+      return last_launch_error();
+    });
+  }
   if (g.any_bc) {  // exterior states at this stage's time t + c_i dt
     timed(E, ES_KERNEL_OTHER, st, [&] { launch_bc_eval(g.bc, t_dev ? t_dev : g.t, t_off, g.bcz, st); });
   }
@@ -631,7 +655,7 @@ int run_stage(Engine& E, Group& g, const StagePrep& sp, const StageVol& sv, cuda
     timed(E, ES_KERNEL_FACE, st,
           [&] { Lc::face(g.P, g.aux, g.F, g.FL, st, grid_for(E, 3LL * g.K * g.P1 * g.P1, 256)); });
     if (ns) timed(E, ES_KERNEL_GRAD, st, [&] { Lc::grad(g.P, g.aux, g.fV, st, grid_for(E, g.N, 256)); });
-    timed(E, ES_KERNEL_VOLUME, st, [&] { Lc::volume(g.P, sv, g.aux, g.F, g.FL, g.fV, ns, st, g.vol_variant); });
+    timed(E, ES_KERNEL_VOLUME, st, [&] { Lc::volume(g.P, sv, g.aux, g.F, g.FL, g.fV, ns, st, g.vol_variant % kVolumeVariants); });
     return last_launch_error();
   });
 }
@@ -657,24 +681,36 @@ StageRelax relax_base(Engine& E, Group& g) {
   const double floor_default = (g.cfg.precision == ES_MIXED || g.cfg.precision == ES_MIXED_FF) ? 4e-6 : 1e-8;
   sr.delta_floor = g.cfg.delta_floor > 0.0 ? g.cfg.delta_floor : floor_default;
   sr.gamma_max = 8.0;
+  // Newton stop: a step |s| <= 1e-8 gamma leaves an error ~s^2/gamma ~ 1e-16 gamma
+  sr.root_rtol = g.cfg.root_rtol > 0.0 ? g.cfg.root_rtol : 1e-8;
   return sr;
 }
 
 // One relaxed step of every instance of the group on state q: all stages, the
 // gamma_kappa solve, gamma = min, t += gamma dt, pending update flag set.  The
 // update u += gamma d itself runs in the next step's first k_prep (or group_finish).
-// hist (device, per instance) receives gamma if not null.
-int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStream_t st) {
+// hist (device, per instance) receives gamma if not null.  With `estimate` the stages
+// also accumulate A (and the entropy-variable increments it needs) when the method
+// relaxes nothing, so that the step's entropy estimate can be formed afterwards.
+int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStream_t st, bool estimate = false) {
   const Tableau& T = E.tab;
   const bool relax = E.relax != ES_RELAX_NONE;
+  const bool acc_A = relax || estimate;
+  const bool fused = stage_fused(g);
   int rc = ES_OK;
+  if (fused) {  // the fused stages read neighbours' states: apply the pending update first
+    timed(E, ES_KERNEL_OTHER, st,
+          [&] { launch_update(g.P, q, q, g.d, g.gamma_cur, g.pending, g.Np, st, grid_for(E, 5 * g.N, 256)); });
+    timed(E, ES_KERNEL_OTHER, st, [&] { launch_reset(g.gmin, g.pending, g.ninst, st); });
+    rc = last_launch_error();
+  }
   for (int i = 0; i < T.s && rc == ES_OK; ++i) {
     StagePrep sp;
     std::memset(&sp, 0, sizeof(sp));
     sp.q = q;
     sp.d = g.d;
     sp.gamma_cur = g.gamma_cur;
-    sp.pending = (i == 0) ? g.pending : nullptr;
+    sp.pending = (i == 0 && !fused) ? g.pending : nullptr;
     sp.Np = g.Np;
     for (int j = 0; j < i; ++j) {
       if (T.a[i][j] != 0.0) {
@@ -683,7 +719,7 @@ int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStre
         sp.nprev++;
       }
     }
-    const bool want_dw = relax && i > 0 && T.b[i] != 0.0;
+    const bool want_dw = acc_A && i > 0 && T.b[i] != 0.0;
     sp.dw = want_dw ? g.dw : nullptr;
     StageVol sv;
     std::memset(&sv, 0, sizeof(sv));
@@ -700,7 +736,7 @@ int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStre
       }
     }
     sv.dw = want_dw ? g.dw : nullptr;
-    sv.A = relax ? g.A : nullptr;
+    sv.A = acc_A ? g.A : nullptr;
     sv.A_scale = -T.b[i];
     sv.A_init = (i == 0);
     rc = run_stage(E, g, sp, sv, st, t, T.c[i] * g.P.g0.dt);
@@ -724,6 +760,7 @@ int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStre
     ga.status = E.status;
     ga.delta_floor = sr.delta_floor;
     ga.gamma_max = sr.gamma_max;
+    ga.root_rtol = sr.root_rtol;
     const int grid = (int)std::min<long long>((g.K + 3) / 4, (long long)E.sm_count * 16);
     rc = dispatch(g, [&](auto L) {
       timed(E, ES_KERNEL_RELAX, st,
@@ -765,6 +802,25 @@ int advance_device(es_ctx* c, double* q, int nsteps, double dt, double* t, doubl
   }
   if (rc == ES_OK && nsteps > 0) rc = group_finish(c->eng, g, q, st);
   return rc;
+}
+
+// The estimate of the step just taken (before its pending update): eta_kappa(u) and
+// deta_kappa (k_estimate) into eta_old / deta (device, K each; either may be null).
+int group_estimate(Engine& E, Group& g, const double* q, double* eta_old, double* deta, cudaStream_t st) {
+  const int grid = (int)std::min<long long>((g.K + 3) / 4, (long long)E.sm_count * 16);
+  return dispatch(g, [&](auto L) {
+    timed(E, ES_KERNEL_OTHER, st, [&] { decltype(L)::estimate(g.P, q, g.d, g.A, eta_old, deta, st, grid); });
+    return last_launch_error();
+  });
+}
+
+// eta_kappa(q) of every element of the group into eta (device, K)
+int group_entropy(Engine& E, Group& g, const double* q, double* eta, cudaStream_t st) {
+  const int grid = (int)std::min<long long>((g.K + 3) / 4, (long long)E.sm_count * 16);
+  return dispatch(g, [&](auto L) {
+    timed(E, ES_KERNEL_OTHER, st, [&] { decltype(L)::entropy(g.P, q, eta, st, grid); });
+    return last_launch_error();
+  });
 }
 
 // Node coordinates [3][K][Np] of the mesh of C (host).
@@ -813,10 +869,12 @@ int autotune_group(Engine& E, Group& g, const double* q, cudaStream_t st) {
   const bool prof = E.profiling;
   E.profiling = false;
   int rc = ES_OK;
-  for (int v = 0; v < kVolumeVariants && rc == ES_OK; ++v) {
+  const int nv = stage_fusable(g) ? kStageVariants : kVolumeVariants;
+  for (int v = 0; v < nv && rc == ES_OK; ++v) {
     g.vol_variant = v;
     float tmin = 1e30f;
     for (int rep = 0; rep < 3 && rc == ES_OK; ++rep) {
+      // a first stage into k[0], then a stage on y = u + dt/2 k[0] that accumulates A
       StagePrep sp;
       std::memset(&sp, 0, sizeof(sp));
       sp.q = const_cast<double*>(q);
@@ -826,6 +884,18 @@ int autotune_group(Engine& E, Group& g, const double* q, cudaStream_t st) {
       sv.kout = g.k[0];
       cudaEventRecord(a, st);
       rc = run_stage(E, g, sp, sv, st);
+      if (rc == ES_OK && g.nk > 1) {
+        sp.nprev = 1;
+        sp.coef[0] = 0.5;
+        sp.k[0] = g.k[0];
+        sp.dw = g.dw;
+        sv.kout = g.k[1];
+        sv.dw = g.dw;
+        sv.A = g.A;
+        sv.A_scale = -0.5;
+        sv.A_init = 1;
+        rc = run_stage(E, g, sp, sv, st);
+      }
       cudaEventRecord(b, st);
       if (rc == ES_OK) rc = cuda_check(cudaEventSynchronize(b));
       float ms = 0.f;
@@ -936,6 +1006,7 @@ int es_set_boundary(es_ctx* c, int dir, int kind, const double* params, int npar
   if (rc != ES_OK) return rc;
   for (int m = 0; m < 3; ++m) g.P.bc[m] = b.kind[m] != ES_BC_PERIODIC ? 1 : 0;
   g.P.bcz = g.bcz;
+  if (g.vol_variant >= kVolumeVariants && !stage_fusable(g)) g.vol_variant -= kVolumeVariants;
   return ES_OK;
 }
 
@@ -1004,6 +1075,23 @@ int es_advance(es_ctx* c, double* q, int nsteps, double dt, double* t, double* g
   return advance_device(c, q, nsteps, dt, t, gamma_hist, gamma_elem, static_cast<cudaStream_t>(stream));
 }
 
+int es_step_estimate(es_ctx* c, double* q, double dt, double* t, double* gamma, double* gamma_elem, double* eta_old,
+                     double* deta, double* eta_new, void* stream) {
+  if (!c || !q || !(dt > 0.0) || !std::isfinite(dt)) return ES_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Engine& E = c->eng;
+  Group& g = c->g;
+  g.P.g0.dt = dt;
+  timed(E, ES_KERNEL_OTHER, st, [&] { launch_reset(g.gmin, g.pending, g.ninst, st); });
+  int rc = group_step(E, g, q, t ? t : g.t, gamma, st, true);
+  if (rc == ES_OK && (eta_old || deta)) rc = group_estimate(E, g, q, eta_old, deta, st);
+  if (rc == ES_OK && gamma_elem)
+    rc = cuda_check(cudaMemcpyAsync(gamma_elem, g.gamma_elem, sizeof(double) * g.K, cudaMemcpyDeviceToDevice, st));
+  if (rc == ES_OK) rc = group_finish(E, g, q, st);
+  if (rc == ES_OK && eta_new) rc = group_entropy(E, g, q, eta_new, st);
+  return rc;
+}
+
 int es_advance_host(es_ctx* c, double* q_host, int nsteps, double dt, double* t_host, double* gamma_hist_host,
                     void* stream) {
   if (!c || !q_host || !t_host || nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return ES_ERR_INVALID;
@@ -1036,6 +1124,15 @@ int es_advance_host(es_ctx* c, double* q_host, int nsteps, double dt, double* t_
 int es_autotune(es_ctx* c, const double* q, void* stream) {
   if (!c || !q) return ES_ERR_INVALID;
   return autotune_group(c->eng, c->g, q, static_cast<cudaStream_t>(stream));
+}
+
+int es_volume_variant(const es_ctx* c) { return c ? c->g.vol_variant : ES_ERR_INVALID; }
+
+int es_set_volume_variant(es_ctx* c, int variant) {
+  if (!c || variant < 0 || variant >= kStageVariants) return ES_ERR_INVALID;
+  if (variant >= kVolumeVariants && !stage_fusable(c->g)) return ES_ERR_INVALID;
+  c->g.vol_variant = variant;
+  return ES_OK;
 }
 
 int es_node_coords(const es_ctx* c, double* xyz) {
@@ -1093,7 +1190,7 @@ namespace {
 bool same_physics(const es_config& a, const es_config& b) {
   return a.gamma_gas == b.gamma_gas && a.mu == b.mu && (a.mu == 0.0 || a.Pr == b.Pr) && a.R == b.R &&
          a.interface_diss == b.interface_diss && a.relax == b.relax && a.rk == b.rk && a.precision == b.precision &&
-         a.delta_floor == b.delta_floor && a.visc_diss == b.visc_diss;
+         a.delta_floor == b.delta_floor && a.visc_diss == b.visc_diss && a.root_rtol == b.root_rtol;
 }
 
 void batch_free(es_batch* b) {
@@ -1301,6 +1398,40 @@ int es_batch_advance(es_batch* b, int nsteps, void* stream) {
   if (rc == ES_OK) rc = cuda_check(cudaEventRecord(ev, b->exec_stream));
   if (rc == ES_OK) rc = cuda_check(cudaStreamWaitEvent(st, ev, 0));
   if (ev) cudaEventDestroy(ev);
+  return rc;
+}
+
+int es_batch_step_estimate(es_batch* b, void* stream) {
+  if (!b) return ES_ERR_INVALID;
+  for (auto& g : b->groups)
+    for (auto& G : g.geom)
+      if (!(G.dt > 0.0)) return ES_ERR_INVALID;  // es_batch_set_dt first
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Engine& E = b->eng;
+  int rc = ES_OK;
+  for (auto& g : b->groups) {
+    if (rc == ES_OK && !g.est) rc = dev_alloc(&g.est, 3 * (size_t)g.K);
+    if (rc == ES_OK) timed(E, ES_KERNEL_OTHER, st, [&] { launch_reset(g.gmin, g.pending, g.ninst, st); });
+    if (rc == ES_OK) rc = group_step(E, g, g.q, g.t, nullptr, st, true);
+    if (rc == ES_OK) rc = group_estimate(E, g, g.q, g.est, g.est + g.K, st);
+    if (rc == ES_OK) rc = group_finish(E, g, g.q, st);
+    if (rc == ES_OK) rc = group_entropy(E, g, g.q, g.est + 2 * (long long)g.K, st);
+  }
+  return rc;
+}
+
+int es_batch_get_estimate(es_batch* b, int inst, double* eta_old_host, double* deta_host, double* eta_new_host,
+                          double* gamma_elem_host) {
+  if (!b || inst < 0 || inst >= (int)b->cfgs.size()) return ES_ERR_INVALID;
+  const Group& g = b->groups[b->where[inst].first];
+  if (!g.est) return ES_ERR_INVALID;  // es_batch_step_estimate first
+  const InstGeom& G = g.geom[b->where[inst].second];
+  const size_t bytes = sizeof(double) * G.nx * G.ny * G.nz;
+  int rc = cuda_check(cudaDeviceSynchronize());
+  const double* src[4] = {g.est, g.est + g.K, g.est + 2 * (long long)g.K, g.gamma_elem};
+  double* dst[4] = {eta_old_host, deta_host, eta_new_host, gamma_elem_host};
+  for (int k = 0; k < 4 && rc == ES_OK; ++k)
+    if (dst[k]) rc = cuda_check(cudaMemcpy(dst[k], src[k] + G.off, bytes, cudaMemcpyDeviceToHost));
   return rc;
 }
 

@@ -278,17 +278,83 @@ __device__ __forceinline__ double to_f64(float x) { return f32_to_f64_bits(x); }
 __device__ __forceinline__ double to_f64(ff x) { return double(x); }
 
 // ---------------------------------------------------------------------------
+// The stage state at one node in the flux precision TF (k_prep stores it; the fused
+// stage kernel k_stage forms it again for its own nodes and its neighbours' face nodes
+// with this same code, so both sides of every face see the same bits).
+//
+// FP64 estimates with FP32 fluxes (ES_MIXED): the stage increment e = dt sum_j a_ij k_j
+// in FP64 (the FP32 k_j placed into FP64 on the integer pipe), y = u + e, and the
+// parameter vector formed from y in float-float and rounded once.
+template <typename TF, int NPREV>
+__device__ __forceinline__ void stage_increment_f64(const Params& P, const StagePrep& sp, long long N, long long g,
+                                                    int inst, double e[5]) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) e[v] = 0.0;
+  if constexpr (NPREV != 0) {
+    const double dt = geom_of(P, inst).dt;
+#pragma unroll
+    for (int j = 0; j < (NPREV >= 0 ? NPREV : sp.nprev); ++j) {
+      const double c = sp.coef[j] * dt;
+      const TF* kj = static_cast<const TF*>(sp.k[j]);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) e[v] = fma(c, to_f64(kj[v * N + g]), e[v]);
+    }
+  }
+}
+template <typename TF>
+__device__ __forceinline__ bool stage_z_f64(const Params& P, const double u[5], const double e[5], TF z[6]) {
+  ff yf[5], zf[6];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) yf[v] = ff_from_double(u[v] + e[v]);
+  const bool ok = param_vector_ff(yf, P.Cff, zf);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) z[c] = tf_from_ff<TF>(zf[c]);
+  return ok;
+}
+
+// Float-float estimates (ES_MIXED_FF, ES_FP64X): u split into float-float (integer
+// pipe), e and y = u + e and the parameter vector in float-float.
+template <typename TF, int NPREV>
+__device__ __forceinline__ void stage_increment_ff(const Params& P, const StagePrep& sp, long long N, long long g,
+                                                   int inst, const double u[5], ff uf[5], ff ef[5]) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    uf[v] = ff_from_double(u[v]);
+    ef[v] = ff(0.0f, 0.0f);
+  }
+  if constexpr (NPREV != 0) {
+    const double dt = geom_of(P, inst).dt;
+#pragma unroll
+    for (int j = 0; j < (NPREV >= 0 ? NPREV : sp.nprev); ++j) {
+      const ff c = ff_from_double(sp.coef[j] * dt);
+      const TF* kj = static_cast<const TF*>(sp.k[j]);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) ff_fma_acc(ef[v], c, to_ff(kj[v * N + g]));
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) ef[v] = ff_norm(ef[v]);
+  }
+}
+template <typename TF, int NPREV>
+__device__ __forceinline__ bool stage_z_ff(const Params& P, const ff uf[5], const ff ef[5], TF z[6]) {
+  ff yf[5], zf[6];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) yf[v] = NPREV != 0 ? uf[v] + ef[v] : uf[v];
+  const bool ok = param_vector_ff(yf, P.Cff, zf);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) z[c] = tf_from_ff<TF>(zf[c]);
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
 // y = u (+ gamma d when the instance has a pending relaxed update and this is the
 // step's first stage) + dt sum_j a_ij k_j over the stages with a_ij != 0.
 // FP64 mode: everything in FP64.  Mixed mode with FP64 estimates (P.ff_est = 0):
-// e = dt sum_j a_ij k_j, y = u + e and w(y) - w(u) in FP64 (the FP32 k_j placed into
-// FP64 on the integer pipe); the parameter vector for the FP32 fluxes is formed from
-// y in float-float and rounded once.  ES_FP64X and the mixed float-float mode: the
-// FP64 state is split into float-float (integer pipe), e, y, the parameter vector and
-// w(y) - w(u) are formed in float-float on the FP32 pipe.  FP64 selects the
-// FP64-increment paths at compile time (they differ widely in register use).
-// NPREV >= 0 fixes the number of earlier stages at compile time; NPREV < 0 reads it
-// from sp.nprev (tableaux with more than three nonzero a_ij in a row).
+// stage_increment_f64 / stage_z_f64 and w(y) - w(u) in FP64.  ES_FP64X and the mixed
+// float-float mode: stage_increment_ff / stage_z_ff and w(y) - w(u) in float-float.
+// FP64 selects the FP64-increment paths at compile time (they differ widely in
+// register use).  NPREV >= 0 fixes the number of earlier stages at compile time;
+// NPREV < 0 reads it from sp.nprev (tableaux with more than three nonzero a_ij in a row).
 template <typename TF, int NPREV, bool FP64>
 __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __restrict__ status) {
   const long long N = (long long)P.K * sp.Np;
@@ -307,23 +373,12 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
       }
     }
     if constexpr (FP64 && !std::is_same<TF, double>::value) {
-      double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      if constexpr (NPREV != 0) {
-        const double dt = geom_of(P, inst).dt;
+      double e[5];
+      stage_increment_f64<TF, NPREV>(P, sp, N, g, inst, e);
+      TF z[6];
+      if (!stage_z_f64<TF>(P, u, e, z)) atomicOr(status, kStatusNonphysical);
 #pragma unroll
-        for (int j = 0; j < (NPREV >= 0 ? NPREV : sp.nprev); ++j) {
-          const double c = sp.coef[j] * dt;
-          const TF* kj = static_cast<const TF*>(sp.k[j]);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) e[v] = fma(c, to_f64(kj[v * N + g]), e[v]);
-        }
-      }
-      ff yf[5], z[6];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) yf[v] = ff_from_double(u[v] + e[v]);
-      if (!param_vector_ff(yf, P.Cff, z)) atomicOr(status, kStatusNonphysical);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) aux[c * N + g] = tf_from_ff<TF>(z[c]);
+      for (int c = 0; c < 6; ++c) aux[c * N + g] = z[c];
       if (sp.dw) {
         double dw[5];
         entropy_var_increment(u, e, gam, P.Cd.inv_gm1, dw);
@@ -367,38 +422,15 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
         for (int v = 0; v < 5; ++v) sp.dw[v * N + g] = dw[v];
       }
     } else {
-      const FluxConst<ff>& C = P.Cff;
-      ff uf[5], ef[5], yf[5];
+      ff uf[5], ef[5];
+      stage_increment_ff<TF, NPREV>(P, sp, N, g, inst, u, uf, ef);
+      TF z[6];
+      if (!stage_z_ff<TF, NPREV>(P, uf, ef, z)) atomicOr(status, kStatusNonphysical);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        uf[v] = ff_from_double(u[v]);
-        ef[v] = ff(0.0f, 0.0f);
-      }
-      if constexpr (NPREV != 0) {
-        const double dt = geom_of(P, inst).dt;
-#pragma unroll
-        for (int j = 0; j < (NPREV >= 0 ? NPREV : sp.nprev); ++j) {
-          const ff c = ff_from_double(sp.coef[j] * dt);
-          const TF* kj = static_cast<const TF*>(sp.k[j]);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) ff_fma_acc(ef[v], c, to_ff(kj[v * N + g]));
-        }
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          ef[v] = ff_norm(ef[v]);
-          yf[v] = uf[v] + ef[v];
-        }
-      } else {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) yf[v] = uf[v];
-      }
-      ff z[6];
-      if (!param_vector_ff(yf, C, z)) atomicOr(status, kStatusNonphysical);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) aux[c * N + g] = tf_from_ff<TF>(z[c]);
+      for (int c = 0; c < 6; ++c) aux[c * N + g] = z[c];
       if (sp.dw) {
         ff dw[5];
-        entropy_var_increment_ff(uf, ef, C, dw);
+        entropy_var_increment_ff(uf, ef, P.Cff, dw);
 #pragma unroll
         for (int v = 0; v < 5; ++v) sp.dw[v * N + g] = double(dw[v]);
       }
@@ -868,7 +900,7 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
         // d = dt (b_i k_i + sum_j b_j k_j): coefficients and dt split on the integer pipe
         const ff dtf = ff_from_double(G.dt);
         const ff cs = ff_from_double(sv.dcoef_self);
-        ff cj[4];
+        ff cj[kMaxStages];  // one per earlier stage with b_j != 0 (sv.nd < kMaxStages)
         for (int j = 0; j < sv.nd; ++j) cj[j] = ff_from_double(sv.dcoef[j]);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
@@ -935,6 +967,290 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
 }
 
 // ---------------------------------------------------------------------------
+// Fused stage for FP32 fluxes on periodic Euler groups (ES_MIXED: FP64E, ES_MIXED_FF:
+// !FP64E): the work of k_prep, k_face and k_volume for one stage in one launch, without
+// the round trips of the parameter vector, the entropy-variable increments and the face
+// fluxes through global memory.  A CTA forms the parameter vector of its EPB elements'
+// nodes and of the neighbours' face nodes its lines end on (the stage_z_* code k_prep
+// uses, so a face node has the same bits in both CTAs), evaluates the interface flux at
+// both ends of each line with k_face's arguments (a face's flux is the same on both of
+// its elements, so the conservation sums still cancel), the flux differencing of
+// k_volume, and its node phase with w(y) - w(u) formed again from u and the stage values.
+// Results are bit-identical to k_prep + k_face + k_volume.  The previous step's relaxed
+// update must have been applied before the launch: a CTA reads its neighbours' states.
+template <int P1, bool FP64E, int NPREV>
+__device__ __forceinline__ bool stage_node_z(const Params& P, const StagePrep& sp, long long N, long long g, int inst,
+                                             float z[6]) {
+  double u[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) u[v] = sp.q[v * N + g];
+  if constexpr (FP64E) {
+    double e[5];
+    stage_increment_f64<float, NPREV>(P, sp, N, g, inst, e);
+    return stage_z_f64<float>(P, u, e, z);
+  } else {
+    ff uf[5], ef[5];
+    stage_increment_ff<float, NPREV>(P, sp, N, g, inst, u, uf, ef);
+    return stage_z_ff<float, NPREV>(P, uf, ef, z);
+  }
+}
+
+template <int P1, int EPB>
+struct StageSmem {
+  static constexpr int P2 = P1 * P1, Np = P1 * P2;
+  static constexpr int HALO = 6 * kAuxPlanes * EPB * P2;  // floats: [dir, side][plane][EPB * P2]
+  static constexpr int RED = 4 * EPB * Np;                // floats of the two FP64 reduction rows
+  static constexpr int UNION = HALO > RED ? HALO : RED;   // the rows reuse the halo after the flux phase
+  static constexpr size_t bytes = size_t(UNION + (kAuxPlanes + 5) * EPB * Np) * sizeof(float);
+};
+
+template <int P1, bool FP64E, int NPREV, int EPB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_stage(Params P, StagePrep sp, StageVol sv, int* __restrict__ status) {
+  using TF = float;
+  using S = StageSmem<P1, EPB>;
+  constexpr int P2 = P1 * P1, Np = P1 * P2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TF* halo = reinterpret_cast<TF*>(smem_raw);
+  double* red = reinterpret_cast<double*>(smem_raw);
+  TF* za = halo + S::UNION;              // [kAuxPlanes][EPB*Np]: z1..z5, 1/z1
+  TF* acc = za + kAuxPlanes * EPB * Np;  // [5][EPB*Np]
+  const long long N = (long long)P.K * Np;
+  const int e0 = blockIdx.x * EPB;
+  const int nel = min(EPB, P.K - e0);
+  const int nn = nel * Np;
+  const FluxConst<TF> C = flux_const<TF>(P);
+  const TF iw = tf_from_double<TF>(P.inv_omega_end);
+
+  // the element tile
+  for (int t = threadIdx.x; t < nn; t += THREADS) {
+    const long long g = (long long)e0 * Np + t;
+    TF z[6];
+    if (!stage_node_z<P1, FP64E, NPREV>(P, sp, N, g, inst_of(P, e0 + t / Np), z)) atomicOr(status, kStatusNonphysical);
+#pragma unroll
+    for (int c = 0; c < kAuxPlanes; ++c) za[c * EPB * Np + t] = z[c];
+  }
+  // neighbour face nodes, h = ((m * 2 + side) * nel + el) * P2 + ab: side 0 is the -x_m
+  // neighbour's last node on line (a, b), side 1 the +x_m neighbour's first
+  const int nh = 6 * nel * P2;
+  for (int h = threadIdx.x; h < nh; h += THREADS) {
+    const int ab = h % P2;
+    const int r = h / P2;
+    const int el = r % nel, ms = r / nel;
+    const int m = ms >> 1, side = ms & 1;
+    const int en = neighbour(P, e0 + el, m, side ? 1 : -1);
+    const long long g = (long long)en * Np + line_node<P1>(m, ab % P1, ab / P1, side ? 0 : P1 - 1);
+    TF z[6];
+    stage_node_z<P1, FP64E, NPREV>(P, sp, N, g, inst_of(P, en), z);  // its own CTA reports a bad state
+#pragma unroll
+    for (int c = 0; c < kAuxPlanes; ++c) halo[(ms * kAuxPlanes + c) * EPB * P2 + el * P2 + ab] = z[c];
+  }
+  __syncthreads();
+
+#pragma unroll 1
+  for (int m = 0; m < 3; ++m) {
+    for (int l = threadIdx.x; l < nel * P2; l += THREADS) {
+      const int el = l / P2, ab = l % P2;
+      const int a = ab % P1, b = ab / P1;
+      const int e = e0 + el;
+      const TF met = tf_from_double<TF>(geom_of(P, inst_of(P, e)).metric[m]);
+      Zstate<TF> z[P1];
+#pragma unroll
+      for (int i = 0; i < P1; ++i) {
+        const int n = el * Np + line_node<P1>(m, a, b, i);
+#pragma unroll
+        for (int c = 0; c < kAux; ++c) z[i].z[c] = za[c * EPB * Np + n];
+      }
+      TF r[P1][5];
+#pragma unroll
+      for (int i = 0; i < P1; ++i)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) r[i][v] = TF(0);
+#pragma unroll
+      for (int i = 0; i < P1; ++i) {
+#pragma unroll
+        for (int j = i + 1; j < P1; ++j) {
+          TF f[5];
+          ec_flux(z[i], z[j], m, C, f);
+          const TF dij = Tab<TF>::D2(P, i * P1 + j), dji = Tab<TF>::D2(P, j * P1 + i);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            fma_acc(r[i][v], dij, f[v]);
+            fma_acc(r[j][v], dji, f[v]);
+          }
+        }
+      }
+      // interface terms: + (1/omega_p) f_num(this, +x_m neighbour) at i = p,
+      // - (1/omega_0) f_num(-x_m neighbour, this) at i = 0
+      {
+        const int nl = el * Np + line_node<P1>(m, a, b, P1 - 1), nf = el * Np + line_node<P1>(m, a, b, 0);
+        const TF* hm = halo + (m * 2) * kAuxPlanes * EPB * P2 + el * P2 + ab;
+        const TF* hp = hm + kAuxPlanes * EPB * P2;
+        Zstate<TF> Lm, Rp;
+#pragma unroll
+        for (int c = 0; c < kAux; ++c) {
+          Lm.z[c] = hm[c * EPB * P2];
+          Rp.z[c] = hp[c * EPB * P2];
+        }
+        TF fp[5], fm[5];
+        face_flux(z[P1 - 1], za[5 * EPB * Np + nl], Rp, hp[5 * EPB * P2], m, C, P.diss, fp);
+        face_flux(Lm, hm[5 * EPB * P2], z[0], za[5 * EPB * Np + nf], m, C, P.diss, fm);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          r[P1 - 1][v] += iw * fp[v];
+          r[0][v] -= iw * fm[v];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < P1; ++i) {
+        const int n = el * Np + line_node<P1>(m, a, b, i);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const TF val = -met * r[i][v];
+          acc[v * EPB * Np + n] = (m == 0) ? val : acc[v * EPB * Np + n] + val;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // node phase (k_volume's, the halo space now holding the reduction rows): k_i or, in
+  // the last stage, d; the element sums with w(y) - w(u) formed again here
+  const bool wantE = sv.E != nullptr;
+  const bool wantA = sv.A != nullptr && sv.dw_inline;
+  for (int t = threadIdx.x; t < nn; t += THREADS) {
+    const long long g = (long long)e0 * Np + t;
+    const int n = t % Np;
+    const int inst = inst_of(P, e0 + t / Np);
+    const InstGeom& G = geom_of(P, inst);
+    double dw[5];
+    if (wantA) {
+      double u[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) u[v] = sp.q[v * N + g];
+      if constexpr (FP64E) {
+        double e[5];
+        stage_increment_f64<TF, NPREV>(P, sp, N, g, inst, e);
+        entropy_var_increment(u, e, P.gam, P.Cd.inv_gm1, dw);
+      } else {
+        ff uf[5], ef[5], dwf[5];
+        stage_increment_ff<TF, NPREV>(P, sp, N, g, inst, u, uf, ef);
+        entropy_var_increment_ff(uf, ef, P.Cff, dwf);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dw[v] = double(dwf[v]);
+      }
+    }
+    if constexpr (FP64E) {
+      const double Pn = mass_weight<P1>(P, G.J, n);
+      double k[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) k[v] = to_f64(acc[v * EPB * Np + t]);
+      if (sv.d_out) {
+        const double dt = G.dt;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          double dv = (sv.dcoef_self * dt) * k[v];
+          for (int j = 0; j < sv.nd; ++j)
+            dv = fma(sv.dcoef[j] * dt, to_f64(static_cast<const TF*>(sv.dk[j])[v * N + g]), dv);
+          sv.d_out[v * N + g] = dv;
+        }
+      } else if (sv.kout64) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sv.kout64[v * N + g] = k[v];
+      } else {
+        TF* ko = static_cast<TF*>(sv.kout);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ko[v * N + g] = acc[v * EPB * Np + t];
+      }
+      if (wantE) {
+        Zstate<TF> s;
+#pragma unroll
+        for (int c = 0; c < kAux; ++c) s.z[c] = za[c * EPB * Np + t];
+        TF w[5];
+        z_to_w(s, C, w);
+        double sum = 0.0;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sum += to_f64(w[v]) * k[v];
+        red[t] = Pn * sum;
+      }
+      if (wantA) {
+        double sum = 0.0;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sum += dw[v] * k[v];
+        red[EPB * Np + t] = Pn * G.dt * sum;
+      }
+    } else {
+      TF kt[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) kt[v] = acc[v * EPB * Np + t];
+      if (sv.d_out) {
+        const ff dtf = ff_from_double(G.dt);
+        const ff cs = ff_from_double(sv.dcoef_self);
+        ff cj[kMaxStages];  // one per earlier stage with b_j != 0 (sv.nd < kMaxStages)
+        for (int j = 0; j < sv.nd; ++j) cj[j] = ff_from_double(sv.dcoef[j]);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          ff dv = cs * to_ff(kt[v]);
+          for (int j = 0; j < sv.nd; ++j) ff_fma_acc(dv, cj[j], to_ff(static_cast<const TF*>(sv.dk[j])[v * N + g]));
+          sv.d_out[v * N + g] = double(ff_norm(dv) * dtf);
+        }
+      } else if (sv.kout64) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sv.kout64[v * N + g] = double(kt[v]);
+      } else {
+        TF* ko = static_cast<TF*>(sv.kout);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ko[v * N + g] = kt[v];
+      }
+      if (wantE) {
+        Zstate<TF> s;
+#pragma unroll
+        for (int c = 0; c < kAux; ++c) s.z[c] = za[c * EPB * Np + t];
+        TF w[5];
+        z_to_w(s, C, w);
+        double sum = 0.0;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sum += double(w[v]) * double(kt[v]);
+        red[t] = mass_weight<P1>(P, G.J, n) * sum;
+      }
+      if (wantA) {
+        ff sum(0.0f, 0.0f);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ff_fma_acc(sum, ff_from_double(dw[v]), to_ff(kt[v]));
+        reinterpret_cast<ff*>(red)[EPB * Np + t] = mass_weight_ff<P1>(P, n) * ff_norm(sum);
+      }
+    }
+  }
+  const bool doA = sv.A != nullptr && (wantA || sv.A_init);
+  if (!wantE && !doA) return;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int el = warp; el < nel; el += THREADS >> 5) {
+    double sE = 0.0, sA = 0.0;
+    for (int n = lane; n < Np; n += 32) {
+      if (wantE) sE += red[el * Np + n];
+      if (FP64E && wantA) sA += red[EPB * Np + el * Np + n];
+    }
+    if (wantE) sE = warp_sum(sE);
+    if (FP64E) {
+      sA = warp_sum(sA);
+    } else if (wantA) {
+      ff s(0.0f, 0.0f);
+      for (int n = lane; n < Np; n += 32) s = s + reinterpret_cast<const ff*>(red)[EPB * Np + el * Np + n];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        s = s + ff(__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o));
+      const InstGeom& G = geom_of(P, inst_of(P, e0 + el));
+      sA = double(s) * (G.J * G.dt);
+    }
+    if (lane == 0) {
+      const int e = e0 + el;
+      if (wantE) sv.E[e] = sE;
+      if (doA) sv.A[e] = (sv.A_init ? 0.0 : sv.A[e]) + (wantA ? sv.A_scale * sA : 0.0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Relaxation (one lane group per element, RelaxGroup).  Per node: X0 = d_rho/rho,
 // dv = (d_m - v d_rho)/rho, Y0 = (gam-1)(d_E - v.d_m + |v|^2 d_rho/2)/p,
 // V2 = rho |dv|^2/p, c = P_n rho.  r(g) = sum_n c D_n(g)/rho_n + g A,
@@ -943,8 +1259,8 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
 // relax_node_cubic), safeguarded by the bracket [lo, hi] (r(lo) <= 0 < r(hi)); r is
 // convex, so Newton converges from above.
 // Near the root the error after a step s is ~ s^2 r''/(2 r') ~ s^2/g, so a step
-// |s| <= 1e-8 g leaves an error ~1e-16 g: the updated iterate is returned
-// without another evaluation.
+// |s| <= root_rtol g (default 1e-8) leaves an error ~1e-16 g: the updated iterate is
+// returned without another evaluation.
 template <int P1>
 __global__ void k_relax(Params P, StageRelax sr) {
   using RG = RelaxGroup<P1>;
@@ -1062,7 +1378,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
           const double step = rv * fast_rcp(dv);
           const double newton = gcur - step;
           // converged: a step this small cannot leave the bracket by more than rounding
-          if (phys && dv > 0.0 && fabs(step) <= 1e-8 * gcur) {
+          if (phys && dv > 0.0 && fabs(step) <= sr.root_rtol * gcur) {
             gk = fmin(fmax(newton, lo), hi);
             break;
           }
@@ -1092,7 +1408,8 @@ __global__ void k_relax(Params P, StageRelax sr) {
 // k_relax in float-float for the mixed and ES_FP64X modes: node data, element sums,
 // bracket and Newton steps on the FP32 pipe (es_ff.cuh; ~2^-47 relative), the root
 // joined to FP64 once per element.  Same rules as k_relax; the bracket-width stop is
-// 2^-44 max(1, gamma) (the float-float resolution) instead of 4 * 2^-52.
+// 2^-44 max(1, gamma) (the float-float resolution) instead of 4 * 2^-52, and the
+// Newton-step tolerance is at least 2^-40.
 // float-float / FP32 sums over a lane group (butterfly within the group's lanes)
 template <int SUB>
 __device__ __forceinline__ ff group_sum_ff(ff v, unsigned mask) {
@@ -1114,6 +1431,9 @@ __global__ void k_relax_ff(Params P, StageRelax sr) {
   const unsigned gmask = RG::mask(lane);
   const int warps_per_block = blockDim.x >> 5;
   const float floor2 = float(sr.delta_floor * sr.delta_floor);
+  // Newton-step stop: the caller's tolerance, not below 2^-40 (float-float steps carry
+  // rounding noise of ~2^-47 gamma; the bracket-width stop 2^-44 ends finer requests)
+  const float rtol = float(fmax(sr.root_rtol, 9.094947017729282e-13));
   const ff gmax = ff_from_double(sr.gamma_max);
   const ff zero(0.0f, 0.0f);
   for (int e = (blockIdx.x * warps_per_block + (threadIdx.x >> 5)) * RG::EPW + lane / SUB; e < P.K;
@@ -1188,7 +1508,7 @@ __global__ void k_relax_ff(Params P, StageRelax sr) {
           }
           const ff step = rv * ff_rcp(dv);
           const ff newton = gcur - step;
-          if (phys && dv.hi > 0.0f && fabsf(step.hi) <= 1e-8f * gcur.hi) {
+          if (phys && dv.hi > 0.0f && fabsf(step.hi) <= rtol * gcur.hi) {
             gk = double(ff_min(ff_max(newton, lo), hi));
             break;
           }
@@ -1323,7 +1643,7 @@ static __global__ void k_gnewton(Params P, GlobalRelaxState* gs, const double* _
                           const double* __restrict__ elem_s, const double* __restrict__ A,
                           const double* __restrict__ elem_r, const double* __restrict__ elem_dr,
                           unsigned long long* gmin_bits, int* status, double delta_floor, double gamma_max,
-                          int phase) {
+                          double root_rtol, int phase) {
   __shared__ double sh[256];
   const int inst = blockIdx.x;
   const InstGeom& G = geom_of(P, inst);
@@ -1373,7 +1693,7 @@ static __global__ void k_gnewton(Params P, GlobalRelaxState* gs, const double* _
     const double step = rv / dv;
     const double newton = gcur - step;
     const bool nok = phys && dv > 0.0 && isfinite(newton) && newton > S.lo && newton < S.hi;
-    if (phys && dv > 0.0 && fabs(step) <= 1e-8 * gcur) {
+    if (phys && dv > 0.0 && fabs(step) <= root_rtol * gcur) {
       S.result = fmin(fmax(newton, S.lo), S.hi);
       S.done = 1;
     } else if (S.hi - S.lo <= 8.881784197001252e-16 * fmax(1.0, gcur)) {
@@ -1423,6 +1743,48 @@ __global__ void k_entropy(Params P, const double* __restrict__ q, double* __rest
     }
     s = warp_sum(s);
     if (lane == 0) eta[e] = s;
+  }
+}
+
+// The two sides of Theorem 2.3's local inequality for the step just taken (state u
+// before its relaxed update, d = u_new - u, A from the stages): eta_old = eta_kappa(u)
+// in the arithmetic of k_entropy, and the estimate
+// deta = eta_kappa^new - eta_kappa(u) = sum_n P_n w(u_n).d_n - A, which equals
+// dt sum_i b_i (eta_kappa' f)(y^i) of Eq. (eta-est-1-RK) because the stages accumulate
+// A = -dt sum_i b_i sum_n P_n (w(y^i) - w(u)).k_i.  One warp per element.
+template <int P1>
+__global__ void k_estimate(Params P, const double* __restrict__ q, const double* __restrict__ d,
+                           const double* __restrict__ A, double* __restrict__ eta_old, double* __restrict__ deta) {
+  constexpr int Np = P1 * P1 * P1;
+  const long long N = (long long)P.K * Np;
+  const double gam = P.gam;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < P.K; e += gridDim.x * wpb) {
+    const double J = geom_of(P, inst_of(P, e)).J;
+    double s_eta = 0.0, s_wd = 0.0;
+    for (int n = lane; n < Np; n += 32) {
+      const long long g = (long long)e * Np + n;
+      const double rho = q[g];
+      const double ir = 1.0 / rho;
+      const double m0 = q[N + g], m1 = q[2 * N + g], m2 = q[3 * N + g];
+      const double p = (gam - 1.0) * (q[4 * N + g] - 0.5 * (m0 * m0 + m1 * m1 + m2 * m2) * ir);
+      const double s = log(p) - gam * log(rho);
+      const double Pn = mass_weight<P1>(P, J, n);
+      s_eta += Pn * (-rho * s / (gam - 1.0));
+      // w = ((gam - s)/(gam-1) - beta |v|^2/2, beta v, -beta), beta = rho/p
+      const double beta = rho / p;
+      const double v0 = m0 * ir, v1 = m1 * ir, v2 = m2 * ir;
+      const double w0 = (gam - s) / (gam - 1.0) - 0.5 * beta * (v0 * v0 + v1 * v1 + v2 * v2);
+      s_wd += Pn * (w0 * d[g] + beta * (v0 * d[N + g] + v1 * d[2 * N + g] + v2 * d[3 * N + g]) -
+                    beta * d[4 * N + g]);
+    }
+    s_eta = warp_sum(s_eta);
+    s_wd = warp_sum(s_wd);
+    if (lane == 0) {
+      if (eta_old) eta_old[e] = s_eta;
+      if (deta) deta[e] = s_wd - A[e];
+    }
   }
 }
 
@@ -1518,6 +1880,66 @@ void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* a
   else volume_v<P1, TF, 0>(P, sv, a, f, fl, v, ns, st);
 }
 
+template <int P1, bool FP64E, int NPREV, int V>
+void stage_launch_v(const Params& P, const StagePrep& sp, const StageVol& sv, int* status, cudaStream_t st) {
+  using C = VolCfg<P1, V>;
+  const int grid = (P.K + C::EPB - 1) / C::EPB;
+  k_stage<P1, FP64E, NPREV, C::EPB, C::THREADS>
+      <<<grid, C::THREADS, StageSmem<P1, C::EPB>::bytes, st>>>(P, sp, sv, status);
+}
+
+template <int P1, bool FP64E, int V>
+void stage_launch_np(const Params& P, const StagePrep& sp, const StageVol& sv, int* status, cudaStream_t st) {
+  if (sp.nprev == 0) stage_launch_v<P1, FP64E, 0, V>(P, sp, sv, status, st);
+  else if (sp.nprev == 1) stage_launch_v<P1, FP64E, 1, V>(P, sp, sv, status, st);
+  else stage_launch_v<P1, FP64E, -1, V>(P, sp, sv, status, st);
+}
+
+template <int P1, bool FP64E, int V>
+cudaError_t stage_setup_v() {
+  using C = VolCfg<P1, V>;
+  const int smem = (int)StageSmem<P1, C::EPB>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(k_stage<P1, FP64E, 0, C::EPB, C::THREADS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_stage<P1, FP64E, 1, C::EPB, C::THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_stage<P1, FP64E, -1, C::EPB, C::THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+  return e;
+}
+
+template <int P1, typename TF>
+cudaError_t Launcher<P1, TF>::stage_setup() {
+  if constexpr (std::is_same<TF, float>::value) {
+    cudaError_t e = stage_setup_v<P1, true, 0>();
+    if (e == cudaSuccess) e = stage_setup_v<P1, true, 1>();
+    if (e == cudaSuccess) e = stage_setup_v<P1, true, 2>();
+    if (e == cudaSuccess) e = stage_setup_v<P1, false, 0>();
+    if (e == cudaSuccess) e = stage_setup_v<P1, false, 1>();
+    if (e == cudaSuccess) e = stage_setup_v<P1, false, 2>();
+    return e;
+  }
+  return cudaSuccess;
+}
+
+template <int P1, typename TF>
+void Launcher<P1, TF>::stage(const Params& P, const StagePrep& sp, const StageVol& sv, int* status, cudaStream_t st,
+                             int variant) {
+  if constexpr (std::is_same<TF, float>::value) {
+    if (!P.ff_est) {
+      if (variant == 1) stage_launch_np<P1, true, 1>(P, sp, sv, status, st);
+      else if (variant == 2) stage_launch_np<P1, true, 2>(P, sp, sv, status, st);
+      else stage_launch_np<P1, true, 0>(P, sp, sv, status, st);
+    } else {
+      if (variant == 1) stage_launch_np<P1, false, 1>(P, sp, sv, status, st);
+      else if (variant == 2) stage_launch_np<P1, false, 2>(P, sp, sv, status, st);
+      else stage_launch_np<P1, false, 0>(P, sp, sv, status, st);
+    }
+  }
+}
+
 template <int P1, typename TF>
 void Launcher<P1, TF>::relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid) {
   // the u_new entry point (es_relax_step), the FP64 mode and the mixed mode with FP64
@@ -1535,11 +1957,11 @@ void Launcher<P1, TF>::global_relax(const Params& P, const GlobalRelaxArgs& ga, 
                                     int iterations) {
   k_gsetup<P1><<<grid, 128, 0, st>>>(P, ga.u, ga.d, ga.nodes, ga.elem_a, ga.elem_s);
   k_gnewton<<<P.ninst, 256, 0, st>>>(P, ga.gs, ga.elem_a, ga.elem_s, ga.A, ga.elem_r, ga.elem_dr, ga.gmin_bits,
-                                      ga.status, ga.delta_floor, ga.gamma_max, 0);
+                                      ga.status, ga.delta_floor, ga.gamma_max, ga.root_rtol, 0);
   for (int it = 0; it < iterations; ++it) {
     k_geval<P1><<<grid, 128, 0, st>>>(P, ga.nodes, ga.gs, ga.elem_r, ga.elem_dr);
     k_gnewton<<<P.ninst, 256, 0, st>>>(P, ga.gs, ga.elem_a, ga.elem_s, ga.A, ga.elem_r, ga.elem_dr, ga.gmin_bits,
-                                        ga.status, ga.delta_floor, ga.gamma_max, 1);
+                                        ga.status, ga.delta_floor, ga.gamma_max, ga.root_rtol, 1);
   }
   k_gfinish<<<(P.K + 255) / 256, 256, 0, st>>>(P, ga.gs, ga.gmin_bits, ga.gamma_elem);
 }
@@ -1547,6 +1969,12 @@ void Launcher<P1, TF>::global_relax(const Params& P, const GlobalRelaxArgs& ga, 
 template <int P1, typename TF>
 void Launcher<P1, TF>::entropy(const Params& P, const double* q, double* eta, cudaStream_t st, int grid) {
   k_entropy<P1><<<grid, 128, 0, st>>>(P, q, eta);
+}
+
+template <int P1, typename TF>
+void Launcher<P1, TF>::estimate(const Params& P, const double* q, const double* d, const double* A, double* eta_old,
+                                double* deta, cudaStream_t st, int grid) {
+  k_estimate<P1><<<grid, 128, 0, st>>>(P, q, d, A, eta_old, deta);
 }
 
 }  // namespace es

@@ -44,6 +44,7 @@ struct StageVol {
   double* A;           // relaxation term accumulator, or nullptr
   double A_scale;      // -b_i (times the instance's dt in the kernel)
   int A_init;          // first stage of the step: A starts at zero
+  int dw_inline;       // k_stage: this stage's w(y) - w(u) enter A (formed in the kernel)
 };
 
 // k_relax inputs/outputs
@@ -59,6 +60,7 @@ struct StageRelax {
   int* status;
   double delta_floor;
   double gamma_max;
+  double root_rtol;        // Newton-step stop |step| <= root_rtol gamma
 };
 
 // global relaxation: per-instance Newton state
@@ -80,11 +82,14 @@ struct GlobalRelaxArgs {
   unsigned long long* gmin_bits;
   double* gamma_elem;
   int* status;
-  double delta_floor, gamma_max;
+  double delta_floor, gamma_max, root_rtol;
 };
 
 constexpr int kGlobalRelaxIterations = 8;
+// volume tiles 0..2: k_prep + k_face + k_volume; 3..5: the same tiles in the fused
+// k_stage (FP32 fluxes on periodic Euler groups only)
 constexpr int kVolumeVariants = 3;
+constexpr int kStageVariants = 2 * kVolumeVariants;
 
 template <int P1, typename TF>
 struct Launcher {
@@ -96,8 +101,15 @@ struct Launcher {
   // variant: volume tile (elements per CTA, threads), 0..kVolumeVariants-1
   static void volume(const Params& P, const StageVol& sv, const void* aux, const void* F, const void* FL,
                      const void* fV, bool ns, cudaStream_t st, int variant);
+  // fused k_prep + k_face + k_volume (TF = float, Euler, periodic; no pending update)
+  static cudaError_t stage_setup();
+  static void stage(const Params& P, const StagePrep& sp, const StageVol& sv, int* status, cudaStream_t st,
+                    int variant);
   static void relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid);
   static void entropy(const Params& P, const double* q, double* eta, cudaStream_t st, int grid);
+  // Theorem 2.3's eta_kappa(u) and estimate deta_kappa = sum P w(u).d - A (either output may be null)
+  static void estimate(const Params& P, const double* q, const double* d, const double* A, double* eta_old,
+                       double* deta, cudaStream_t st, int grid);
   static void global_relax(const Params& P, const GlobalRelaxArgs& ga, cudaStream_t st, int grid, int iterations);
 };
 

@@ -43,7 +43,7 @@ def load_checkpoint(path):
 class Solver:
     def __init__(self, p, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0,
                  interface_diss=1, relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64,
-                 delta_floor=0.0, device="cuda", visc_diss=0.0):
+                 delta_floor=0.0, device="cuda", visc_diss=0.0, root_rtol=0.0):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -55,7 +55,7 @@ class Solver:
         self.K = self.n[0] * self.n[1] * self.n[2]
         self.N = self.K * self.Np
         self.cfg = B.make_config(p, n, lo, hi, gamma_gas, mu, Pr, R, interface_diss, relax, rk, precision,
-                                 delta_floor, visc_diss)
+                                 delta_floor, visc_diss, root_rtol)
         with torch.cuda.device(self.device):
             self.ctx = B.es_create(self.cfg)
 
@@ -111,6 +111,21 @@ class Solver:
         B.es_advance(self.ctx, q, nsteps, dt, t, hist, gk, stream)
         return t, hist, gk
 
+    def step_estimate(self, q, dt, t=None, stream=None):
+        """One relaxed step (in place on q) returning the per-element quantities of the
+        local entropy inequality: dict of device tensors eta_old, deta, eta_new, gamma_elem
+        and the step's gamma (es_step_estimate)."""
+        torch = self.torch
+        out = {k: torch.empty(self.K, dtype=torch.float64, device=self.device)
+               for k in ("eta_old", "deta", "eta_new", "gamma_elem")}
+        out["gamma"] = torch.empty(1, dtype=torch.float64, device=self.device)
+        if t is None:
+            t = torch.zeros(1, dtype=torch.float64, device=self.device)
+        B.es_step_estimate(self.ctx, q, dt, t, out["gamma"], out["gamma_elem"], out["eta_old"], out["deta"],
+                           out["eta_new"], stream)
+        out["t"] = t
+        return out
+
     def advance_host(self, q_host, nsteps, dt, t_host, hist_host=None, stream=None):
         B.es_advance_host(self.ctx, q_host, nsteps, dt, t_host, hist_host, stream)
 
@@ -125,7 +140,7 @@ class Solver:
         return {"p": c.p, "n": [c.nx, c.ny, c.nz], "lo": list(c.lo), "hi": list(c.hi), "gamma_gas": c.gamma_gas,
                 "mu": c.mu, "Pr": c.Pr, "R": c.R, "interface_diss": c.interface_diss, "relax": c.relax,
                 "rk": c.rk, "precision": c.precision, "delta_floor": c.delta_floor, "visc_diss": c.visc_diss,
-                "tableau": getattr(self, "tableau", None)}
+                "root_rtol": c.root_rtol, "tableau": getattr(self, "tableau", None)}
 
     def checkpoint(self, path, q, t, step, dt):
         """Write the device state q, time t (float) and step counter to path (see save_checkpoint)."""
@@ -139,7 +154,7 @@ class Solver:
         c = h["config"]
         s = cls(c["p"], tuple(c["n"]), tuple(c["lo"]), tuple(c["hi"]), c["gamma_gas"], c["mu"], c["Pr"], c["R"],
                 c["interface_diss"], c["relax"], c["rk"], c["precision"], c["delta_floor"], device=device,
-                visc_diss=c.get("visc_diss", 0.0))
+                visc_diss=c.get("visc_diss", 0.0), root_rtol=c.get("root_rtol", 0.0))
         if c.get("tableau"):
             s.set_tableau(c["tableau"]["A"], c["tableau"]["b"], c["tableau"]["c"])
         return s, s.to_device(q), h["t"], h["step"], h["dt"]
@@ -162,6 +177,14 @@ class Solver:
 
     def autotune(self, q, stream=None):
         B.es_autotune(self.ctx, q, stream)
+
+    def volume_variant(self):
+        return B.es_volume_variant(self.ctx)
+
+    def set_volume_variant(self, variant):
+        """0..2: k_prep + k_face + k_volume tiles; 3..5: the fused stage kernel (FP32
+        fluxes, periodic Euler); every variant gives the same bits."""
+        B.es_set_volume_variant(self.ctx, variant)
 
     def profile(self, enable):
         B.es_profile_enable(self.ctx, enable)
@@ -191,11 +214,12 @@ class BatchSolver:
     """Many independent instances (possibly different degrees and element counts)."""
 
     def __init__(self, instances, gamma_gas=1.4, mu=0.0, Pr=0.72, R=1.0, interface_diss=1,
-                 relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64, delta_floor=0.0, visc_diss=0.0):
+                 relax=B.ES_RELAX_LOCAL, rk=B.ES_RK_BS3, precision=B.ES_FP64, delta_floor=0.0, visc_diss=0.0,
+                 root_rtol=0.0):
         """instances: list of dicts with p, n (nx, ny, nz), lo, hi."""
         self.cfgs = [B.make_config(d["p"], d["n"], d.get("lo", (0.0, 0.0, 0.0)), d.get("hi", (1.0, 1.0, 1.0)),
                                    gamma_gas, mu, Pr, R, interface_diss, relax, rk, precision, delta_floor,
-                                   visc_diss)
+                                   visc_diss, root_rtol)
                      for d in instances]
         self.instances = instances
         self.count = len(instances)
@@ -247,6 +271,18 @@ class BatchSolver:
 
     def advance(self, nsteps, stream=None):
         B.es_batch_advance(self.b, nsteps, stream)
+
+    def step_estimate(self, stream=None):
+        """One relaxed step of every instance keeping the local entropy inequality's
+        quantities (es_batch_step_estimate); read them with get_estimate(i)."""
+        B.es_batch_step_estimate(self.b, stream)
+
+    def get_estimate(self, i):
+        """dict of host arrays eta_old, deta, eta_new, gamma_elem of instance i."""
+        K = self.shape(i)[1]
+        out = {k: np.empty(K) for k in ("eta_old", "deta", "eta_new", "gamma_elem")}
+        B.es_batch_get_estimate(self.b, i, out["eta_old"], out["deta"], out["eta_new"], out["gamma_elem"])
+        return out
 
     def times(self):
         t = np.zeros(self.count)

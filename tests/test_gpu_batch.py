@@ -62,6 +62,10 @@ def build_batch(insts, precision=0):
 
 
 def test_batch_against_oracle():
+    """Every instance against the oracle run alone: state at 1e-12 per variable, t at
+    1e-12, and gamma at 1e-12 or 8x its response to rounding-level right-hand-side
+    changes where that is larger."""
+    import oracle_jobs as J
     insts = instances(6)
     assert len({d["p"] for d in insts}) >= 3          # several degree groups
     nsteps = 5
@@ -78,7 +82,9 @@ def test_batch_against_oracle():
         err = np.max(np.abs(q.reshape(5, -1) - ref), axis=1) / scale
         assert np.all(err < TOL), (i, err)
         assert abs(t_gpu[i] - t) < TOL * t
-        assert abs(g_gpu[i] - hist[-1].gamma) < 1e-10 * hist[-1].gamma
+        sens_g, _ = J.gamma_sensitivity(mesh, U, dt, nsteps, dg.Physics(G, diss=1), rk.BS3, "local", hist, seeds=2)
+        assert abs(g_gpu[i] - hist[-1].gamma) <= max(TOL, 8 * sens_g[-1]) * hist[-1].gamma, \
+            (i, g_gpu[i], hist[-1].gamma, sens_g[-1])
     b.close()
 
 
