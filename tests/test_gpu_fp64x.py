@@ -58,6 +58,14 @@ def test_fp64x_advance_vortex_4cubed_p3():
     assert np.all(np.abs(g - 1) < 0.1)
 
 
+def test_fp64x_root_rtol_below_float_float_resolution():
+    """A root_rtol far below the float-float resolution (the oracle's 4 * 2^-52) is
+    clamped to 2^-40 in the float-float solve: it ends and meets the FP64X bars."""
+    mesh, U, lo, hi = vortex_setup()
+    compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=1), "BS3", 6, eps=EPS_FF, precision=_fp64x(),
+                    root_rtol=4 * 2.0 ** -52)
+
+
 def test_fp64x_advance_rk4_ec_ragged():
     mesh, U, lo, hi = vortex_setup(N=5, p=2, nz=3)
     compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=0), "RK4", 6, eps=EPS_FF, precision=_fp64x())

@@ -161,6 +161,15 @@ def test_advance_vortex_4cubed_p3():
     assert np.all(np.abs(g - 1) < 0.1)
 
 
+def test_advance_root_rtol_at_oracle_tolerance():
+    """es_config.root_rtol = 4 * 2^-52, the oracle's own stop: the CUDA solve then stops
+    on the same rule as the oracle's and meets the same bars (FP64); the float-float
+    solve clamps the request to 2^-40 and meets its bars too (test_gpu_fp64x)."""
+    mesh, U, lo, hi = vortex_setup()
+    g = compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=1), "BS3", 8, root_rtol=4 * EPS)
+    assert np.all(np.abs(g - 1) < 0.1)
+
+
 def test_advance_rk4_ec_ragged():
     mesh, U, lo, hi = vortex_setup(N=5, p=2, nz=3)
     compare_advance(mesh, U, lo, hi, dg.Physics(G, diss=0), "RK4", 6)
