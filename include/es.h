@@ -270,10 +270,11 @@ int es_autotune(es_ctx* ctx, const double* q, void* stream);
 
 /* The tile variant in use: 0..2 run the stage as k_prep + k_face + k_volume with one
  * of three (elements per CTA x threads) tiles of the flux-differencing kernel; 3..5
- * run the same tiles as one fused kernel per stage (available for FP32 fluxes,
- * ES_MIXED and ES_MIXED_FF, on periodic Euler meshes, where it is the default), which
- * forms the parameter vector and the interface fluxes on chip instead of storing them.
- * Every variant gives bit-identical results.  es_set_volume_variant returns
+ * use the same tiles with the interface fluxes evaluated inside the flux-differencing
+ * kernel from the neighbours' parameter vectors, so the face-flux kernel and its
+ * round trip through memory drop out (available for FP32 fluxes, ES_MIXED and
+ * ES_MIXED_FF, on periodic Euler meshes; each face's flux is then evaluated by both
+ * of its elements).  Every variant gives bit-identical results; 0 is the default.  es_set_volume_variant returns
  * ES_ERR_INVALID for a variant outside 0..5 or a fused one the context cannot use;
  * es_autotune picks among all usable variants. */
 int es_volume_variant(const es_ctx* ctx);

@@ -277,7 +277,8 @@ struct Group {
   double* est = nullptr;                 // batch estimate step: eta_old, deta, eta_new [3][K]
 };
 
-// The fused stage kernel serves FP32 fluxes (ES_MIXED, ES_MIXED_FF) on periodic Euler groups.
+// The volume kernel with on-chip interface fluxes serves FP32 fluxes (ES_MIXED, ES_MIXED_FF)
+// on periodic Euler groups.
 bool stage_fusable(const Group& g) { return g.tf == 4 && g.cfg.mu == 0.0 && !g.any_bc; }
 bool stage_fused(const Group& g) { return g.vol_variant >= kVolumeVariants && stage_fusable(g); }
 
@@ -563,8 +564,7 @@ int group_init(Group& g, const es_config* insts, int n, int stages, bool own_sta
     rc = cuda_check(cudaDeviceSynchronize());
   }
   if (rc == ES_OK) rc = dispatch(g, [&](auto L) { return cuda_check(decltype(L)::volume_setup()); });
-  if (rc == ES_OK) rc = dispatch(g, [&](auto L) { return cuda_check(decltype(L)::stage_setup()); });
-  if (stage_fusable(g)) g.vol_variant = kVolumeVariants;  // fused, default tile
+  if (rc == ES_OK) rc = dispatch(g, [&](auto L) { return cuda_check(decltype(L)::volface_setup()); });
   return rc;
 }
 
@@ -627,22 +627,17 @@ void launch_bc_eval(const BcSpec& spec, const double* t, double t_off, double* o
 int grid_for(const Engine& e, long long n, int block) { return grid_for_sms(e.sm_count, n, block); }
 
 // One stage's right-hand side into kout or d (+ element sums), on state u (+ pending
-// update) + dt sum_j coef[j] k[j].  With a fused variant (stage_fused) one k_stage launch
-// replaces k_prep, k_face and k_volume; it forms the entropy-variable increments itself
-// (sp.dw / sv.dw only say that this stage needs them) and cannot apply a pending update.
+// update) + dt sum_j coef[j] k[j].  With a fused variant (stage_fused) the volume kernel
+// forms the interface fluxes itself and k_face is not launched.
 int run_stage(Engine& E, Group& g, const StagePrep& sp, const StageVol& sv, cudaStream_t st,
               const double* t_dev = nullptr, double t_off = 0.0) {
   const bool ns = g.cfg.mu != 0.0;
   if (stage_fused(g)) {
-    if (sp.pending) return ES_ERR_INVALID;
-    StagePrep sp2 = sp;
-    sp2.dw = nullptr;
-    StageVol sv2 = sv;
-    sv2.dw_inline = sv.dw != nullptr;
-    sv2.dw = nullptr;
     return dispatch(g, [&](auto L) {
+      using Lc = decltype(L);
+      timed(E, ES_KERNEL_PREP, st, [&] { Lc::prep(g.P, sp, g.aux, E.status, st, grid_for(E, g.N, 256)); });
       timed(E, ES_KERNEL_VOLUME, st,
-            [&] { decltype(L)::stage(g.P, sp2, sv2, E.status, st, g.vol_variant - kVolumeVariants); });
+            [&] { Lc::volface(g.P, sv, g.aux, st, g.vol_variant - kVolumeVariants); });
       return last_launch_error();
     });
   }
@@ -696,21 +691,14 @@ int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStre
   const Tableau& T = E.tab;
   const bool relax = E.relax != ES_RELAX_NONE;
   const bool acc_A = relax || estimate;
-  const bool fused = stage_fused(g);
   int rc = ES_OK;
-  if (fused) {  // the fused stages read neighbours' states: apply the pending update first
-    timed(E, ES_KERNEL_OTHER, st,
-          [&] { launch_update(g.P, q, q, g.d, g.gamma_cur, g.pending, g.Np, st, grid_for(E, 5 * g.N, 256)); });
-    timed(E, ES_KERNEL_OTHER, st, [&] { launch_reset(g.gmin, g.pending, g.ninst, st); });
-    rc = last_launch_error();
-  }
   for (int i = 0; i < T.s && rc == ES_OK; ++i) {
     StagePrep sp;
     std::memset(&sp, 0, sizeof(sp));
     sp.q = q;
     sp.d = g.d;
     sp.gamma_cur = g.gamma_cur;
-    sp.pending = (i == 0 && !fused) ? g.pending : nullptr;
+    sp.pending = (i == 0) ? g.pending : nullptr;
     sp.Np = g.Np;
     for (int j = 0; j < i; ++j) {
       if (T.a[i][j] != 0.0) {

@@ -278,9 +278,7 @@ __device__ __forceinline__ double to_f64(float x) { return f32_to_f64_bits(x); }
 __device__ __forceinline__ double to_f64(ff x) { return double(x); }
 
 // ---------------------------------------------------------------------------
-// The stage state at one node in the flux precision TF (k_prep stores it; the fused
-// stage kernel k_stage forms it again for its own nodes and its neighbours' face nodes
-// with this same code, so both sides of every face see the same bits).
+// The stage state at one node in the flux precision TF (k_prep's per-node work).
 //
 // FP64 estimates with FP32 fluxes (ES_MIXED): the stage increment e = dt sum_j a_ij k_j
 // in FP64 (the FP32 k_j placed into FP64 on the integer pipe), y = u + e, and the
@@ -739,16 +737,44 @@ __global__ void __launch_bounds__(THREADS) k_grad(Params P, const TF* __restrict
 }
 
 // ---------------------------------------------------------------------------
-template <int P1, typename TF, bool NS, int EPB, int THREADS>
+// Shared memory of k_volume: the FP64 reduction rows of the node phase (first, so they
+// stay 8-byte aligned), with FACES the neighbours' face-node parameter vectors in the
+// same space (they are dead once the flux phase ends), then the element tile's
+// parameter vector (kAux planes; with FACES also 1/z1) and the accumulator.
+template <int P1, int EPB, bool FACES>
+struct VolSmem {
+  static constexpr int P2 = P1 * P1, Np = P1 * P2;
+  static constexpr int ZP = FACES ? kAuxPlanes : kAux;
+  static constexpr size_t red = size_t(2) * EPB * Np * sizeof(double);
+  static constexpr size_t halo_floats = FACES ? size_t(6) * kAuxPlanes * EPB * P2 : 0;
+  template <typename TF>
+  static constexpr size_t head() {
+    return red > halo_floats * sizeof(TF) ? red : ((halo_floats * sizeof(TF) + 15) / 16) * 16;
+  }
+  template <typename TF>
+  static constexpr size_t bytes() {
+    return head<TF>() + size_t(EPB) * Np * (ZP + 5) * sizeof(TF);
+  }
+};
+
+// Flux differencing, interface terms and viscous divergence of EPB elements per CTA,
+// one LGL line per thread and direction, then the node phase (k_i or d, element sums).
+// FACES (FP32 fluxes on periodic Euler groups): the interface flux at both ends of each
+// line is evaluated here from the neighbours' face-node parameter vectors, with
+// k_face's arguments (the same bits on both elements of a face), instead of being read
+// from F: one launch less per stage and no face-flux round trip through global memory.
+template <int P1, typename TF, bool NS, int EPB, int THREADS, bool FACES = false>
 __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const TF* __restrict__ aux,
                                                    const TF* __restrict__ F, const TF* __restrict__ FL,
                                                    const TF* __restrict__ fV) {
+  using S = VolSmem<P1, EPB, FACES>;
   constexpr int P2 = P1 * P1, Np = P1 * P2;
+  constexpr int ZP = S::ZP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // the FP64 reduction rows first: they stay 8-byte aligned whatever EPB * Np and TF
-  double* red = reinterpret_cast<double*>(smem_raw);   // [2][EPB*Np]
-  TF* za = reinterpret_cast<TF*>(red + 2 * EPB * Np);  // [kAux][EPB*Np]
-  TF* acc = za + kAux * EPB * Np;                       // [5][EPB*Np]
+  double* red = reinterpret_cast<double*>(smem_raw);               // [2][EPB*Np]
+  TF* halo = reinterpret_cast<TF*>(smem_raw);                      // FACES: [dir, side][plane][EPB*P2]
+  TF* za = reinterpret_cast<TF*>(smem_raw + S::template head<TF>());  // [ZP][EPB*Np]
+  TF* acc = za + ZP * EPB * Np;                                    // [5][EPB*Np]
   const long long N = (long long)P.K * Np;
   const int e0 = blockIdx.x * EPB;
   const int nel = min(EPB, P.K - e0);
@@ -758,7 +784,22 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
 
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
 #pragma unroll
-    for (int c = 0; c < kAux; ++c) za[c * EPB * Np + t] = aux[c * N + (long long)e0 * Np + t];
+    for (int c = 0; c < ZP; ++c) za[c * EPB * Np + t] = aux[c * N + (long long)e0 * Np + t];
+  }
+  if constexpr (FACES) {
+    // h = ((m * 2 + side) * nel + el) * P2 + ab: side 0 is the -x_m neighbour's last node
+    // on line (a, b), side 1 the +x_m neighbour's first
+    const int nh = 6 * nel * P2;
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+      const int ab = h % P2;
+      const int r = h / P2;
+      const int el = r % nel, ms = r / nel;
+      const int m = ms >> 1, side = ms & 1;
+      const int en = neighbour(P, e0 + el, m, side ? 1 : -1);
+      const long long g = (long long)en * Np + line_node<P1>(m, ab % P1, ab / P1, side ? 0 : P1 - 1);
+#pragma unroll
+      for (int c = 0; c < kAuxPlanes; ++c) halo[(ms * kAuxPlanes + c) * EPB * P2 + el * P2 + ab] = aux[c * N + g];
+    }
   }
   __syncthreads();
 
@@ -798,12 +839,33 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
       // interface terms: + (1/omega_p) f_num(+face) at i = p, - (1/omega_0) f_num(-face) at i = 0
       // the -x_m face flux: the -x_m neighbour's +x_m flux, or the boundary flux in FL
       const bool lo_b = at_boundary(P, e, m, 0);
-      const TF* Fm = lo_b ? FL : F;
       const int em = lo_b ? e : neighbour(P, e, m, -1);
+      if constexpr (FACES) {
+        // f_num(this element, +x_m neighbour) and f_num(-x_m neighbour, this element)
+        const int nl = el * Np + line_node<P1>(m, a, b, P1 - 1), nf = el * Np + line_node<P1>(m, a, b, 0);
+        const TF* hm = halo + (m * 2) * kAuxPlanes * EPB * P2 + el * P2 + ab;
+        const TF* hp = hm + kAuxPlanes * EPB * P2;
+        Zstate<TF> Lm, Rp;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        r[P1 - 1][v] += iw * F[((long long)(m * 5 + v) * P.K + e) * P2 + ab];
-        r[0][v] -= iw * Fm[((long long)(m * 5 + v) * P.K + em) * P2 + ab];
+        for (int c = 0; c < kAux; ++c) {
+          Lm.z[c] = hm[c * EPB * P2];
+          Rp.z[c] = hp[c * EPB * P2];
+        }
+        TF fp[5], fm[5];
+        face_flux(z[P1 - 1], za[5 * EPB * Np + nl], Rp, hp[5 * EPB * P2], m, C, P.diss, fp);
+        face_flux(Lm, hm[5 * EPB * P2], z[0], za[5 * EPB * Np + nf], m, C, P.diss, fm);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          r[P1 - 1][v] += iw * fp[v];
+          r[0][v] -= iw * fm[v];
+        }
+      } else {
+        const TF* Fm = lo_b ? FL : F;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          r[P1 - 1][v] += iw * F[((long long)(m * 5 + v) * P.K + e) * P2 + ab];
+          r[0][v] -= iw * Fm[((long long)(m * 5 + v) * P.K + em) * P2 + ab];
+        }
       }
       if constexpr (NS) {
         // viscous divergence (2/h_m)[D F^V_m + lifting]; enters with the opposite sign of r
@@ -948,290 +1010,6 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
     }
     if (wantE) sE = warp_sum(sE);
     if (fp64_sums) {
-      sA = warp_sum(sA);
-    } else if (wantA) {
-      ff s(0.0f, 0.0f);
-      for (int n = lane; n < Np; n += 32) s = s + reinterpret_cast<const ff*>(red)[EPB * Np + el * Np + n];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-        s = s + ff(__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o));
-      const InstGeom& G = geom_of(P, inst_of(P, e0 + el));
-      sA = double(s) * (G.J * G.dt);
-    }
-    if (lane == 0) {
-      const int e = e0 + el;
-      if (wantE) sv.E[e] = sE;
-      if (doA) sv.A[e] = (sv.A_init ? 0.0 : sv.A[e]) + (wantA ? sv.A_scale * sA : 0.0);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Fused stage for FP32 fluxes on periodic Euler groups (ES_MIXED: FP64E, ES_MIXED_FF:
-// !FP64E): the work of k_prep, k_face and k_volume for one stage in one launch, without
-// the round trips of the parameter vector, the entropy-variable increments and the face
-// fluxes through global memory.  A CTA forms the parameter vector of its EPB elements'
-// nodes and of the neighbours' face nodes its lines end on (the stage_z_* code k_prep
-// uses, so a face node has the same bits in both CTAs), evaluates the interface flux at
-// both ends of each line with k_face's arguments (a face's flux is the same on both of
-// its elements, so the conservation sums still cancel), the flux differencing of
-// k_volume, and its node phase with w(y) - w(u) formed again from u and the stage values.
-// Results are bit-identical to k_prep + k_face + k_volume.  The previous step's relaxed
-// update must have been applied before the launch: a CTA reads its neighbours' states.
-template <int P1, bool FP64E, int NPREV>
-__device__ __forceinline__ bool stage_node_z(const Params& P, const StagePrep& sp, long long N, long long g, int inst,
-                                             float z[6]) {
-  double u[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) u[v] = sp.q[v * N + g];
-  if constexpr (FP64E) {
-    double e[5];
-    stage_increment_f64<float, NPREV>(P, sp, N, g, inst, e);
-    return stage_z_f64<float>(P, u, e, z);
-  } else {
-    ff uf[5], ef[5];
-    stage_increment_ff<float, NPREV>(P, sp, N, g, inst, u, uf, ef);
-    return stage_z_ff<float, NPREV>(P, uf, ef, z);
-  }
-}
-
-template <int P1, int EPB>
-struct StageSmem {
-  static constexpr int P2 = P1 * P1, Np = P1 * P2;
-  static constexpr int HALO = 6 * kAuxPlanes * EPB * P2;  // floats: [dir, side][plane][EPB * P2]
-  static constexpr int RED = 4 * EPB * Np;                // floats of the two FP64 reduction rows
-  static constexpr int UNION = HALO > RED ? HALO : RED;   // the rows reuse the halo after the flux phase
-  static constexpr size_t bytes = size_t(UNION + (kAuxPlanes + 5) * EPB * Np) * sizeof(float);
-};
-
-template <int P1, bool FP64E, int NPREV, int EPB, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_stage(Params P, StagePrep sp, StageVol sv, int* __restrict__ status) {
-  using TF = float;
-  using S = StageSmem<P1, EPB>;
-  constexpr int P2 = P1 * P1, Np = P1 * P2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TF* halo = reinterpret_cast<TF*>(smem_raw);
-  double* red = reinterpret_cast<double*>(smem_raw);
-  TF* za = halo + S::UNION;              // [kAuxPlanes][EPB*Np]: z1..z5, 1/z1
-  TF* acc = za + kAuxPlanes * EPB * Np;  // [5][EPB*Np]
-  const long long N = (long long)P.K * Np;
-  const int e0 = blockIdx.x * EPB;
-  const int nel = min(EPB, P.K - e0);
-  const int nn = nel * Np;
-  const FluxConst<TF> C = flux_const<TF>(P);
-  const TF iw = tf_from_double<TF>(P.inv_omega_end);
-
-  // the element tile
-  for (int t = threadIdx.x; t < nn; t += THREADS) {
-    const long long g = (long long)e0 * Np + t;
-    TF z[6];
-    if (!stage_node_z<P1, FP64E, NPREV>(P, sp, N, g, inst_of(P, e0 + t / Np), z)) atomicOr(status, kStatusNonphysical);
-#pragma unroll
-    for (int c = 0; c < kAuxPlanes; ++c) za[c * EPB * Np + t] = z[c];
-  }
-  // neighbour face nodes, h = ((m * 2 + side) * nel + el) * P2 + ab: side 0 is the -x_m
-  // neighbour's last node on line (a, b), side 1 the +x_m neighbour's first
-  const int nh = 6 * nel * P2;
-  for (int h = threadIdx.x; h < nh; h += THREADS) {
-    const int ab = h % P2;
-    const int r = h / P2;
-    const int el = r % nel, ms = r / nel;
-    const int m = ms >> 1, side = ms & 1;
-    const int en = neighbour(P, e0 + el, m, side ? 1 : -1);
-    const long long g = (long long)en * Np + line_node<P1>(m, ab % P1, ab / P1, side ? 0 : P1 - 1);
-    TF z[6];
-    stage_node_z<P1, FP64E, NPREV>(P, sp, N, g, inst_of(P, en), z);  // its own CTA reports a bad state
-#pragma unroll
-    for (int c = 0; c < kAuxPlanes; ++c) halo[(ms * kAuxPlanes + c) * EPB * P2 + el * P2 + ab] = z[c];
-  }
-  __syncthreads();
-
-#pragma unroll 1
-  for (int m = 0; m < 3; ++m) {
-    for (int l = threadIdx.x; l < nel * P2; l += THREADS) {
-      const int el = l / P2, ab = l % P2;
-      const int a = ab % P1, b = ab / P1;
-      const int e = e0 + el;
-      const TF met = tf_from_double<TF>(geom_of(P, inst_of(P, e)).metric[m]);
-      Zstate<TF> z[P1];
-#pragma unroll
-      for (int i = 0; i < P1; ++i) {
-        const int n = el * Np + line_node<P1>(m, a, b, i);
-#pragma unroll
-        for (int c = 0; c < kAux; ++c) z[i].z[c] = za[c * EPB * Np + n];
-      }
-      TF r[P1][5];
-#pragma unroll
-      for (int i = 0; i < P1; ++i)
-#pragma unroll
-        for (int v = 0; v < 5; ++v) r[i][v] = TF(0);
-#pragma unroll
-      for (int i = 0; i < P1; ++i) {
-#pragma unroll
-        for (int j = i + 1; j < P1; ++j) {
-          TF f[5];
-          ec_flux(z[i], z[j], m, C, f);
-          const TF dij = Tab<TF>::D2(P, i * P1 + j), dji = Tab<TF>::D2(P, j * P1 + i);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            fma_acc(r[i][v], dij, f[v]);
-            fma_acc(r[j][v], dji, f[v]);
-          }
-        }
-      }
-      // interface terms: + (1/omega_p) f_num(this, +x_m neighbour) at i = p,
-      // - (1/omega_0) f_num(-x_m neighbour, this) at i = 0
-      {
-        const int nl = el * Np + line_node<P1>(m, a, b, P1 - 1), nf = el * Np + line_node<P1>(m, a, b, 0);
-        const TF* hm = halo + (m * 2) * kAuxPlanes * EPB * P2 + el * P2 + ab;
-        const TF* hp = hm + kAuxPlanes * EPB * P2;
-        Zstate<TF> Lm, Rp;
-#pragma unroll
-        for (int c = 0; c < kAux; ++c) {
-          Lm.z[c] = hm[c * EPB * P2];
-          Rp.z[c] = hp[c * EPB * P2];
-        }
-        TF fp[5], fm[5];
-        face_flux(z[P1 - 1], za[5 * EPB * Np + nl], Rp, hp[5 * EPB * P2], m, C, P.diss, fp);
-        face_flux(Lm, hm[5 * EPB * P2], z[0], za[5 * EPB * Np + nf], m, C, P.diss, fm);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          r[P1 - 1][v] += iw * fp[v];
-          r[0][v] -= iw * fm[v];
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < P1; ++i) {
-        const int n = el * Np + line_node<P1>(m, a, b, i);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const TF val = -met * r[i][v];
-          acc[v * EPB * Np + n] = (m == 0) ? val : acc[v * EPB * Np + n] + val;
-        }
-      }
-    }
-    __syncthreads();
-  }
-
-  // node phase (k_volume's, the halo space now holding the reduction rows): k_i or, in
-  // the last stage, d; the element sums with w(y) - w(u) formed again here
-  const bool wantE = sv.E != nullptr;
-  const bool wantA = sv.A != nullptr && sv.dw_inline;
-  for (int t = threadIdx.x; t < nn; t += THREADS) {
-    const long long g = (long long)e0 * Np + t;
-    const int n = t % Np;
-    const int inst = inst_of(P, e0 + t / Np);
-    const InstGeom& G = geom_of(P, inst);
-    double dw[5];
-    if (wantA) {
-      double u[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) u[v] = sp.q[v * N + g];
-      if constexpr (FP64E) {
-        double e[5];
-        stage_increment_f64<TF, NPREV>(P, sp, N, g, inst, e);
-        entropy_var_increment(u, e, P.gam, P.Cd.inv_gm1, dw);
-      } else {
-        ff uf[5], ef[5], dwf[5];
-        stage_increment_ff<TF, NPREV>(P, sp, N, g, inst, u, uf, ef);
-        entropy_var_increment_ff(uf, ef, P.Cff, dwf);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) dw[v] = double(dwf[v]);
-      }
-    }
-    if constexpr (FP64E) {
-      const double Pn = mass_weight<P1>(P, G.J, n);
-      double k[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) k[v] = to_f64(acc[v * EPB * Np + t]);
-      if (sv.d_out) {
-        const double dt = G.dt;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          double dv = (sv.dcoef_self * dt) * k[v];
-          for (int j = 0; j < sv.nd; ++j)
-            dv = fma(sv.dcoef[j] * dt, to_f64(static_cast<const TF*>(sv.dk[j])[v * N + g]), dv);
-          sv.d_out[v * N + g] = dv;
-        }
-      } else if (sv.kout64) {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sv.kout64[v * N + g] = k[v];
-      } else {
-        TF* ko = static_cast<TF*>(sv.kout);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) ko[v * N + g] = acc[v * EPB * Np + t];
-      }
-      if (wantE) {
-        Zstate<TF> s;
-#pragma unroll
-        for (int c = 0; c < kAux; ++c) s.z[c] = za[c * EPB * Np + t];
-        TF w[5];
-        z_to_w(s, C, w);
-        double sum = 0.0;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sum += to_f64(w[v]) * k[v];
-        red[t] = Pn * sum;
-      }
-      if (wantA) {
-        double sum = 0.0;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sum += dw[v] * k[v];
-        red[EPB * Np + t] = Pn * G.dt * sum;
-      }
-    } else {
-      TF kt[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) kt[v] = acc[v * EPB * Np + t];
-      if (sv.d_out) {
-        const ff dtf = ff_from_double(G.dt);
-        const ff cs = ff_from_double(sv.dcoef_self);
-        ff cj[kMaxStages];  // one per earlier stage with b_j != 0 (sv.nd < kMaxStages)
-        for (int j = 0; j < sv.nd; ++j) cj[j] = ff_from_double(sv.dcoef[j]);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          ff dv = cs * to_ff(kt[v]);
-          for (int j = 0; j < sv.nd; ++j) ff_fma_acc(dv, cj[j], to_ff(static_cast<const TF*>(sv.dk[j])[v * N + g]));
-          sv.d_out[v * N + g] = double(ff_norm(dv) * dtf);
-        }
-      } else if (sv.kout64) {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sv.kout64[v * N + g] = double(kt[v]);
-      } else {
-        TF* ko = static_cast<TF*>(sv.kout);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) ko[v * N + g] = kt[v];
-      }
-      if (wantE) {
-        Zstate<TF> s;
-#pragma unroll
-        for (int c = 0; c < kAux; ++c) s.z[c] = za[c * EPB * Np + t];
-        TF w[5];
-        z_to_w(s, C, w);
-        double sum = 0.0;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sum += double(w[v]) * double(kt[v]);
-        red[t] = mass_weight<P1>(P, G.J, n) * sum;
-      }
-      if (wantA) {
-        ff sum(0.0f, 0.0f);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) ff_fma_acc(sum, ff_from_double(dw[v]), to_ff(kt[v]));
-        reinterpret_cast<ff*>(red)[EPB * Np + t] = mass_weight_ff<P1>(P, n) * ff_norm(sum);
-      }
-    }
-  }
-  const bool doA = sv.A != nullptr && (wantA || sv.A_init);
-  if (!wantE && !doA) return;
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int el = warp; el < nel; el += THREADS >> 5) {
-    double sE = 0.0, sA = 0.0;
-    for (int n = lane; n < Np; n += 32) {
-      if (wantE) sE += red[el * Np + n];
-      if (FP64E && wantA) sA += red[EPB * Np + el * Np + n];
-    }
-    if (wantE) sE = warp_sum(sE);
-    if (FP64E) {
       sA = warp_sum(sA);
     } else if (wantA) {
       ff s(0.0f, 0.0f);
@@ -1834,7 +1612,7 @@ void Launcher<P1, TF>::grad(const Params& P, const void* aux, void* fV, cudaStre
 
 template <int P1, int EPB>
 constexpr size_t vol_smem_bytes(size_t tf) {
-  return size_t(EPB) * P1 * P1 * P1 * ((kAux + 5) * tf + 2 * sizeof(double));
+  return size_t(EPB) * P1 * P1 * P1 * ((kAux + 5) * tf + 2 * sizeof(double));  // VolSmem<P1, EPB, false>
 }
 
 template <int P1, typename TF, int V>
@@ -1880,63 +1658,41 @@ void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* a
   else volume_v<P1, TF, 0>(P, sv, a, f, fl, v, ns, st);
 }
 
-template <int P1, bool FP64E, int NPREV, int V>
-void stage_launch_v(const Params& P, const StagePrep& sp, const StageVol& sv, int* status, cudaStream_t st) {
+template <int P1, int V>
+cudaError_t volface_setup_v() {
   using C = VolCfg<P1, V>;
-  const int grid = (P.K + C::EPB - 1) / C::EPB;
-  k_stage<P1, FP64E, NPREV, C::EPB, C::THREADS>
-      <<<grid, C::THREADS, StageSmem<P1, C::EPB>::bytes, st>>>(P, sp, sv, status);
-}
-
-template <int P1, bool FP64E, int V>
-void stage_launch_np(const Params& P, const StagePrep& sp, const StageVol& sv, int* status, cudaStream_t st) {
-  if (sp.nprev == 0) stage_launch_v<P1, FP64E, 0, V>(P, sp, sv, status, st);
-  else if (sp.nprev == 1) stage_launch_v<P1, FP64E, 1, V>(P, sp, sv, status, st);
-  else stage_launch_v<P1, FP64E, -1, V>(P, sp, sv, status, st);
-}
-
-template <int P1, bool FP64E, int V>
-cudaError_t stage_setup_v() {
-  using C = VolCfg<P1, V>;
-  const int smem = (int)StageSmem<P1, C::EPB>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_stage<P1, FP64E, 0, C::EPB, C::THREADS>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_stage<P1, FP64E, 1, C::EPB, C::THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_stage<P1, FP64E, -1, C::EPB, C::THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
-  return e;
+  return cudaFuncSetAttribute(k_volume<P1, float, false, C::EPB, C::THREADS, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)VolSmem<P1, C::EPB, true>::template bytes<float>());
 }
 
 template <int P1, typename TF>
-cudaError_t Launcher<P1, TF>::stage_setup() {
+cudaError_t Launcher<P1, TF>::volface_setup() {
   if constexpr (std::is_same<TF, float>::value) {
-    cudaError_t e = stage_setup_v<P1, true, 0>();
-    if (e == cudaSuccess) e = stage_setup_v<P1, true, 1>();
-    if (e == cudaSuccess) e = stage_setup_v<P1, true, 2>();
-    if (e == cudaSuccess) e = stage_setup_v<P1, false, 0>();
-    if (e == cudaSuccess) e = stage_setup_v<P1, false, 1>();
-    if (e == cudaSuccess) e = stage_setup_v<P1, false, 2>();
+    cudaError_t e = volface_setup_v<P1, 0>();
+    if (e == cudaSuccess) e = volface_setup_v<P1, 1>();
+    if (e == cudaSuccess) e = volface_setup_v<P1, 2>();
     return e;
   }
   return cudaSuccess;
 }
 
+template <int P1, int V>
+void volface_v(const Params& P, const StageVol& sv, const float* aux, cudaStream_t st) {
+  using C = VolCfg<P1, V>;
+  const int grid = (P.K + C::EPB - 1) / C::EPB;
+  k_volume<P1, float, false, C::EPB, C::THREADS, true>
+      <<<grid, C::THREADS, VolSmem<P1, C::EPB, true>::template bytes<float>(), st>>>(P, sv, aux, nullptr, nullptr,
+                                                                                     nullptr);
+}
+
 template <int P1, typename TF>
-void Launcher<P1, TF>::stage(const Params& P, const StagePrep& sp, const StageVol& sv, int* status, cudaStream_t st,
-                             int variant) {
+void Launcher<P1, TF>::volface(const Params& P, const StageVol& sv, const void* aux, cudaStream_t st, int variant) {
   if constexpr (std::is_same<TF, float>::value) {
-    if (!P.ff_est) {
-      if (variant == 1) stage_launch_np<P1, true, 1>(P, sp, sv, status, st);
-      else if (variant == 2) stage_launch_np<P1, true, 2>(P, sp, sv, status, st);
-      else stage_launch_np<P1, true, 0>(P, sp, sv, status, st);
-    } else {
-      if (variant == 1) stage_launch_np<P1, false, 1>(P, sp, sv, status, st);
-      else if (variant == 2) stage_launch_np<P1, false, 2>(P, sp, sv, status, st);
-      else stage_launch_np<P1, false, 0>(P, sp, sv, status, st);
-    }
+    const float* a = static_cast<const float*>(aux);
+    if (variant == 1) volface_v<P1, 1>(P, sv, a, st);
+    else if (variant == 2) volface_v<P1, 2>(P, sv, a, st);
+    else volface_v<P1, 0>(P, sv, a, st);
   }
 }
 

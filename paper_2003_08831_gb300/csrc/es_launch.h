@@ -44,7 +44,6 @@ struct StageVol {
   double* A;           // relaxation term accumulator, or nullptr
   double A_scale;      // -b_i (times the instance's dt in the kernel)
   int A_init;          // first stage of the step: A starts at zero
-  int dw_inline;       // k_stage: this stage's w(y) - w(u) enter A (formed in the kernel)
 };
 
 // k_relax inputs/outputs
@@ -86,8 +85,8 @@ struct GlobalRelaxArgs {
 };
 
 constexpr int kGlobalRelaxIterations = 8;
-// volume tiles 0..2: k_prep + k_face + k_volume; 3..5: the same tiles in the fused
-// k_stage (FP32 fluxes on periodic Euler groups only)
+// volume tiles 0..2: k_prep + k_face + k_volume; 3..5: k_prep + k_volume with the
+// interface fluxes formed in the volume kernel (FP32 fluxes on periodic Euler groups)
 constexpr int kVolumeVariants = 3;
 constexpr int kStageVariants = 2 * kVolumeVariants;
 
@@ -101,10 +100,9 @@ struct Launcher {
   // variant: volume tile (elements per CTA, threads), 0..kVolumeVariants-1
   static void volume(const Params& P, const StageVol& sv, const void* aux, const void* F, const void* FL,
                      const void* fV, bool ns, cudaStream_t st, int variant);
-  // fused k_prep + k_face + k_volume (TF = float, Euler, periodic; no pending update)
-  static cudaError_t stage_setup();
-  static void stage(const Params& P, const StagePrep& sp, const StageVol& sv, int* status, cudaStream_t st,
-                    int variant);
+  // k_volume with the interface fluxes evaluated in the kernel (TF = float, Euler, periodic)
+  static cudaError_t volface_setup();
+  static void volface(const Params& P, const StageVol& sv, const void* aux, cudaStream_t st, int variant);
   static void relax(const Params& P, const StageRelax& sr, cudaStream_t st, int grid);
   static void entropy(const Params& P, const double* q, double* eta, cudaStream_t st, int grid);
   // Theorem 2.3's eta_kappa(u) and estimate deta_kappa = sum P w(u).d - A (either output may be null)

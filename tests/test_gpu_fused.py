@@ -1,11 +1,12 @@
-"""The fused stage kernel (k_stage: parameter vector, interface fluxes, flux
-differencing and node phase of one stage in one launch, FP32 fluxes on periodic
-Euler meshes) against the unfused k_prep + k_face + k_volume: bit-identical right-hand
-sides, element sums, relaxed advances and batches, on ragged meshes that span several
-tiles with a ragged last one (p = 2..5; both mixed modes; entropy-conservative,
-Rusanov and matrix interface dissipation).  Parity of the mixed modes with the oracle
-is covered by the tests of test_gpu_parity.py, test_gpu_batch.py and
-test_gpu_fullsize.py, which run the fused kernel by default."""
+"""The volume kernel with on-chip interface fluxes (tile variants 3..5: k_volume
+evaluates the interface flux at both ends of each line from the neighbours' parameter
+vectors, and k_face is not launched; FP32 fluxes on periodic Euler meshes) against
+k_prep + k_face + k_volume (variants 0..2): bit-identical right-hand sides, element
+sums, relaxed advances and batches, on ragged meshes that span several tiles with a
+ragged last one (p = 2..5; both mixed modes; entropy-conservative, Rusanov and matrix
+interface dissipation).  The mixed modes' parity with the oracle is covered by the
+tests of test_gpu_parity.py, test_gpu_batch.py and test_gpu_fullsize.py on the
+default variant 0, which these tests tie to 3..5 bit for bit."""
 import numpy as np
 import pytest
 
@@ -39,7 +40,7 @@ def test_fused_rhs_bit_identical(p, n, diss, precision):
     lo, hi = (0.0, 0.0, 0.0), (2 * np.pi,) * 3
     U = state(p, n, lo, hi, seed=p)
     s = Solver(p, n, lo, hi, precision=precision, interface_diss=diss)
-    assert s.volume_variant() >= 3            # fused by default for this configuration
+    assert s.volume_variant() == 0
     q = s.to_device(U)
     out = {}
     for v in range(6):
@@ -76,8 +77,9 @@ def test_fused_advance_bit_identical(p, n, diss, precision):
 
 
 def test_fused_variant_availability():
-    """The fused kernel serves FP32 fluxes on periodic Euler meshes only: FP64, FP64X and
-    Navier--Stokes contexts reject it, boundaries fall back to the unfused tile."""
+    """The on-chip interface fluxes serve FP32 fluxes on periodic Euler meshes only: FP64,
+    FP64X and Navier--Stokes contexts reject the variants, boundaries fall back to the
+    same tile with k_face."""
     from paper_2003_08831_gb300 import _binding as B
     from paper_2003_08831_gb300.solver import Solver
     lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
@@ -98,8 +100,9 @@ def test_fused_variant_availability():
 
 @pytest.mark.parametrize("precision", [1, 3])
 def test_fused_batch_equals_unfused_contexts(precision):
-    """A mixed batch (degrees 2..5, fused by default, autotuned) against each instance in
-    its own context on the unfused tile 0: bit-identical states after 3 steps."""
+    """A mixed batch (degrees 2..5, autotuned over all six variants) against each
+    instance in its own context on tile 0 with k_face: bit-identical states after 3
+    steps."""
     from paper_2003_08831_gb300.solver import BatchSolver, Solver, stable_dt
     params = inputs.batch_instances(8, seed=5, nmin=2, nmax=4)
     insts = [dict(p=d["p"], n=(d["n"],) * 3, lo=(0.0, 0.0, 0.0), hi=(d["box"],) * 3) for d in params]
