@@ -127,6 +127,120 @@ def fp_peak_tflops(precision, sm_mhz):
     return 152 * per_clk * sm_mhz * 1e6 / 1e12
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the
+    recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json copy bandwidth)"
+    except Exception:
+        return 6800.0, "fallback (no MEASURED_PEAKS.json)"
+
+
+def measure_alu_peaks(gpu_index=None):
+    """FP64 and FP32 FMA-chain throughput of this GPU (es_fma_peak), with the SM clock
+    sampled while the probe runs."""
+    from paper_2003_08831_gb300 import _binding as B
+    sampler = ClockSampler(gpu_index).start() if gpu_index is not None else None
+    fp64 = max(B.es_fma_peak(True) for _ in range(2))
+    fp32 = max(B.es_fma_peak(False) for _ in range(2))
+    clk = sampler.stop() if sampler is not None else None
+    return {"fp64_tflops": fp64, "fp32_tflops": fp32, "sm_mhz": clk["sm_mhz"] if clk else None,
+            "how": "es_fma_peak: independent FMA chains, 8 per thread, 64 warps per SM, best of 2 x 5 launches"}
+
+
+# Arithmetic of each part of each kernel per precision mode: "f64", "f32" or "ff"
+# (float-float on the FP32 pipe).  ES_MIXED keeps the stage combination, the entropy
+# increments, d and the sums and the gamma solve in FP64; ES_MIXED_FF and ES_FP64X form
+# them in float-float; the parameter vector is float-float in every mode but FP64.
+ARITH = {
+    0: {"z": "f64", "comb": "f64", "dw": "f64", "flux": "f64", "sums": "f64", "relax": "f64"},
+    1: {"z": "ff", "comb": "f64", "dw": "f64", "flux": "f32", "sums": "f64", "relax": "f64"},
+    2: {"z": "ff", "comb": "ff", "dw": "ff", "flux": "ff", "sums": "ff", "relax": "ff"},
+    3: {"z": "ff", "comb": "ff", "dw": "ff", "flux": "f32", "sums": "ff", "relax": "ff"},
+}
+# FP32 instructions per float-float operation, counted from es_ff.cuh: a sum is a TwoSum
+# (6) + 2 additions + a Fast2Sum (3) = 11, a product 1 + 3 fmas + a Fast2Sum = 7, the
+# accumulating product 12; the flux and thermodynamics mix sums and products about
+# evenly: 9.  A float-float operation occupies the FP32 pipe like 9 FFMAs, i.e. 18 of
+# the peak's flops.
+FF_INSTR_PER_OP = 9.0
+TF_BYTES = {0: 8, 1: 4, 2: 8, 3: 4}
+
+
+def kernel_work(p, n_el, precision, ns=False, stages=3):
+    """Per kernel kind, averaged over the launches of one BS3 step: algorithmic flops split
+    by arithmetic ({"f64": .., "f32": .., "ff": ..}) and the bytes the kernel must move
+    (its inputs and outputs in this design: state and d in FP64, stage values,
+    parameter vector and face fluxes in the flux precision)."""
+    P1 = p + 1
+    Np = P1 ** 3
+    nodes = n_el * Np
+    tf = TF_BYTES[precision]
+    ar = ARITH[precision]
+    nprev = [0, 1, 1]                       # BS3: a21, a32 (a31 = 0)
+    dw_stage = [False, True, True]          # entropy increments where b_i != 0, i > 1
+    out = {}
+
+    def add(d, kind, val):
+        d[kind] = d.get(kind, 0.0) + val
+
+    # k_prep
+    fl, by = {}, 0.0
+    for i in range(stages):
+        add(fl, ar["z"], nodes * PREP_FLOPS_Z)
+        add(fl, ar["comb"], nodes * (PREP_FLOPS_PER_STAGE * nprev[i] + (PREP_FLOPS_PENDING if i == 0 else 0)))
+        if dw_stage[i]:
+            add(fl, ar["dw"], nodes * PREP_FLOPS_DW)
+        by += nodes * (40 + 5 * tf * nprev[i] + 6 * tf + (80 if i == 0 else 0) + (40 if dw_stage[i] else 0))
+    out["prep"] = ({k: v / stages for k, v in fl.items()}, by / stages)
+    # k_face: 3 K P1^2 face-node pairs, both sides' z and 1/z1 read, the flux written
+    fn = 3 * n_el * P1 * P1
+    out["face"] = ({ar["flux"]: fn * FACE_FLOPS_PER_FACE_NODE}, fn * 17 * tf)
+    # k_volume
+    fl, by = {}, 0.0
+    for i in range(stages):
+        wa = dw_stage[i]
+        f = volume_flops_per_element(p, ns, wa) * n_el
+        sums = (12 * Np * n_el if wa else 0) + (10 * 2 * Np * n_el if i == stages - 1 else 0)
+        add(fl, ar["flux"], f - (12 * Np * n_el if wa else 0))
+        add(fl, ar["sums"], sums)
+        b = nodes * 5 * tf + n_el * 30 * P1 * P1 * tf + (40 * nodes if wa else 0)
+        b += (40 + 2 * 5 * tf) * nodes if i == stages - 1 else 5 * tf * nodes
+        if ns:
+            b += 12 * tf * nodes
+        by += b
+    out["volume"] = ({k: v / stages for k, v in fl.items()}, by / stages)
+    out["relax"] = ({ar["relax"]: nodes * (RELAX_FLOPS_SETUP + RELAX_FLOPS_EVAL)}, 80.0 * nodes)
+    if ns:
+        out["grad"] = ({ar["flux"]: nodes * (4 + 3 * (8 * P1 + 4 + 24.0 / P1) + 90)}, nodes * (5 + 12) * tf)
+    return out
+
+
+def kernel_rooflines(p, n_el, precision, prof, peaks, ns=False):
+    """Per kernel kind: the time its algorithmic work needs at the measured peaks --
+    the FP64 pipe (FP64 flops) and the FP32 pipe (FP32 flops, float-float operations at
+    FF_INSTR_PER_OP instructions each) run side by side, HBM at the measured copy
+    bandwidth -- against its average event-timed launch; frac = roofline time / launch
+    time and bound = the unit that sets the roofline time."""
+    hbm, _ = hbm_peak_gbs()
+    out = {}
+    for k, (fl, by) in kernel_work(p, n_el, precision, ns).items():
+        ms, n = prof.get(k, (0.0, 0))
+        if not n:
+            continue
+        t = ms / n * 1e-3
+        t64 = fl.get("f64", 0.0) / (peaks["fp64_tflops"] * 1e12)
+        t32 = (fl.get("f32", 0.0) + 2.0 * FF_INSTR_PER_OP * fl.get("ff", 0.0)) / (peaks["fp32_tflops"] * 1e12)
+        tb = by / (hbm * 1e9)
+        troof = max(t64, t32, tb)
+        bound = "fp64" if troof == t64 else ("fp32" if troof == t32 else "hbm")
+        out[k] = {"avg_launch_ms": ms / n, "flops": {a: v for a, v in fl.items()}, "bytes": by,
+                  "frac_fp64": t64 / t, "frac_fp32": t32 / t, "frac_hbm": tb / t,
+                  "bound": bound, "frac": troof / t}
+    return out
+
+
 # ---------------------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
@@ -473,9 +587,9 @@ def measure_e2e(wl, steps, warmup):
 
 
 # ---------------------------------------------------------------------------------------
-def oracle_sample(steps_or_seconds, by_time=True, ne=6):
-    """The FP64 CPU oracle on a periodic ne^3-element sub-box of the TGV workload (same p,
-    element size and state), full relaxed BS3 steps.  Returns (DOF*stage/s, steps, seconds)."""
+def oracle_setup(ne=6):
+    """A periodic ne^3-element sub-box of the TGV workload (same p, element size and
+    state): (mesh, U, phys, dt)."""
     from oracle import dg, rk
     from paper_2003_08831_gb300 import inputs
     p, N = 3, 32
@@ -484,38 +598,71 @@ def oracle_sample(steps_or_seconds, by_time=True, ne=6):
     x, y, z = mesh.coords()
     U = inputs.tgv_state(x, y, z, mach=0.1)
     phys = dg.Physics(1.4, diss=1)
-    dt = rk.stable_dt(mesh, U, phys, 0.5)
+    return mesh, U, phys, rk.stable_dt(mesh, U, phys, 0.5)
+
+
+_BARRIER = None
+
+
+def _oracle_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_worker(job):
+    """One host core: `warmup` untimed steps, then (after every worker is ready) full
+    relaxed BS3 steps for `amount` seconds (by_time) or steps; returns (steps, seconds,
+    nodes)."""
+    amount, by_time, warmup, ne = job
+    from oracle import rk
+    mesh, U, phys, dt = oracle_setup(ne)
+    for _ in range(warmup):
+        U = rk.rk_step(mesh, U, dt, phys, rk.BS3).U
+    _BARRIER.wait()
     n = 0
     t0 = time.perf_counter()
     while True:
-        r = rk.rk_step(mesh, U, dt, phys, rk.BS3)
-        U = r.U
+        U = rk.rk_step(mesh, U, dt, phys, rk.BS3).U
         n += 1
         el = time.perf_counter() - t0
-        if (by_time and el >= steps_or_seconds) or (not by_time and n >= steps_or_seconds):
+        if (by_time and el >= amount) or (not by_time and n >= amount):
             break
-    nodes = mesh.K * mesh.Np
-    return nodes * STAGES * n / el, n, el, nodes
+    return n, el, mesh.K * mesh.Np
 
 
-def cpu_cores_used():
-    return 1  # numpy elementwise kernels run on one thread
+def oracle_parallel(amount, by_time=True, warmup=1, ne=6, cores=None):
+    """The FP64 CPU oracle, as it stands, on every host core: one spawned process per core,
+    each advancing its own independent periodic ne^3-element sub-box of the TGV workload;
+    the timed loops start together.  Returns (DOF*stage/s summed over the cores, total
+    steps, longest timed loop in s, nodes per sub-box, cores)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=ctx, initializer=_oracle_init,
+                                initargs=(barrier,)) as ex:
+        res = list(ex.map(_oracle_worker, [(amount, by_time, warmup, ne)] * cores))
+    nodes = res[0][2]
+    rate = sum(nodes * STAGES * n / el for n, el, _ in res)
+    return rate, sum(n for n, _, _ in res), max(el for _, el, _ in res), nodes, cores
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        oracle_sample(1, by_time=False)
-    value, n, el, nodes = oracle_sample(args.steps, by_time=False)
-    sample = "periodic 6^3-element sub-box (%d nodes) of the 32^3 p=3 Euler TGV, full relaxed BS3 steps" % nodes
+    value, n, el, nodes, cores = oracle_parallel(args.steps, by_time=False, warmup=args.warmup)
+    sample = ("%d independent periodic 6^3-element sub-boxes (%d nodes each) of the 32^3 p=3 Euler TGV, one per "
+              "host core, %d full relaxed BS3 steps each" % (cores, nodes, args.steps))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (closed-form Taylor-Green vortex, Mach 0.1)",
         "config": workload_config(MAIN),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -544,6 +691,20 @@ def main():
     return run_full(args, rank, world, local_rank)
 
 
+def compact(form):
+    """The few numbers of a form that the end of the JSON line repeats."""
+    out = {"value": form["value"], "ms_per_step": form["ms_per_step"]}
+    kr = form.get("kernel_roofline") or {}
+    if "volume" in kr:
+        out["volume_frac"] = round(kr["volume"]["frac"], 3)
+        out["volume_bound"] = kr["volume"]["bound"]
+    if "speedup_vs_fp64_same_physics" in form:
+        out["speedup_vs_fp64"] = round(form["speedup_vs_fp64_same_physics"], 3)
+    if "error_vs_fp64" in form:
+        out["rel_l2_vs_fp64"] = form["error_vs_fp64"]["rel_l2"]
+    return out
+
+
 def run_full(args, rank, world, local_rank):
     import torch
     import __graft_entry__
@@ -555,10 +716,10 @@ def run_full(args, rank, world, local_rank):
         dist = tdist
     __graft_entry__.build()
     wl = WORKLOADS[args.workload]
+    peaks = None if args.quick else measure_alu_peaks(local_rank)
     res = measure_device(wl, args.steps, args.warmup, dist=dist, clocks_gpu=local_rank)
     ms, units = aggregate(res["ms"], res["nodes"] * STAGES * args.steps, dist, "cuda")
     clocks = res.pop("clocks", None)
-    nodes = res["nodes"]
     value = units / (ms / 1e3)
     if args.quick:
         res["solver"].close()
@@ -586,6 +747,7 @@ def run_full(args, rank, world, local_rank):
     achieved = fl / (avg_ms * 1e-3) / 1e12
     sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
     peak = fp_peak_tflops(wl["precision"], sm_mhz)
+    peak_meas = peaks["fp64_tflops"] if wl["precision"] == 0 else peaks["fp32_tflops"]
     tot = sum(v[0] for v in prof.values())
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -604,16 +766,20 @@ def run_full(args, rank, world, local_rank):
                      "peak_source": "%s ALU peak from unit counts x median SM clock (%.0f MHz): 152 SMs x %s"
                                     % ("FP64" if wl["precision"] == 0 else "FP32", sm_mhz,
                                        "2 DFMA/clk" if wl["precision"] == 0 else "128 FFMA/clk"),
+                     "peak_measured": peak_meas, "frac_of_measured": achieved / peak_meas,
+                     "peak_measured_source": "FMA-chain throughput in this run (es_fma_peak)",
                      "flops_per_launch": fl, "avg_launch_ms": avg_ms},
         "kernel_share": {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1] > 0},
-        "kernel_roofline": kernel_roofline(p, K, wl, prof, peak, fl),
+        "kernel_roofline": kernel_rooflines(p, K, wl["precision"], prof, peaks, ns),
         "clocks": clocks,
+        "peaks_measured": dict(peaks, hbm_gbs=hbm_peak_gbs()[0], hbm_source=hbm_peak_gbs()[1]),
     }
     if world == 1 and not args.no_cpu:
-        v, n, el, nn = oracle_sample(10.0, by_time=True)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-                               "sample": "periodic 6^3-element sub-box (%d nodes) of the workload's mesh and "
-                                         "state, %d full relaxed BS3 steps in %.1f s" % (nn, n, el)}
+        v, nsteps, el, nn, cores = oracle_parallel(10.0)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "%d independent periodic 6^3-element sub-boxes (%d nodes each) of the "
+                                         "workload's mesh and state, one per host core, %d full relaxed BS3 steps "
+                                         "in total in %.1f s" % (cores, nn, nsteps, el)}
     out["e2e"] = measure_e2e(wl, min(args.steps, 20), 3)
     if world == 1 and not args.no_forms:
         forms = {}
@@ -631,15 +797,11 @@ def run_full(args, rank, world, local_rank):
                            "ms_per_step": r2["ms"] / steps2, "steps": steps2,
                            "gamma_range": [r2["gamma_min"], r2["gamma_max"]], "launches": int(r2["launches"]),
                            "kernel_share": {k: round(v[0] / t2, 4) for k, v in p2.items() if v[1] > 0},
+                           "kernel_roofline": kernel_rooflines(w2["p"], w2["n"] ** 3, w2["precision"], p2, peaks,
+                                                               w2["mu"] > 0),
                            "speedup_vs_fp64_same_physics": None}
             if err is not None:
                 forms[name]["error_vs_fp64"] = err
-            if w2["precision"] == 0:      # per-kernel fractions of the FP64 ALU peak
-                n2 = w2["n"] ** 3
-                ns2 = w2["mu"] > 0
-                vf = n2 * (volume_flops_per_element(w2["p"], ns2, False)
-                           + 2 * volume_flops_per_element(w2["p"], ns2, True)) / 3.0
-                forms[name]["kernel_roofline"] = kernel_roofline(w2["p"], n2, w2, p2, peak, vf)
             del r2
         forms["viscous_shock_ns_p3_25^3_fp64"] = measure_shock(0)
         forms["viscous_shock_ns_p3_25^3_fp64x"] = measure_shock(2)
@@ -663,6 +825,19 @@ def run_full(args, rank, world, local_rank):
             if forms[k].get("speedup_vs_fp64_same_physics", 0) is None:
                 del forms[k]["speedup_vs_fp64_same_physics"]
         out["forms"] = forms
+        # the FP64 vs mixed pair on the largest single-instance workload (Navier--Stokes TGV,
+        # 32^3, p = 4) and the other forms, repeated compactly at the end of the line
+        out["ns_fp64"] = compact(forms["tgv_ns_re1600_p4_32^3_fp64"])
+        out["ns_mixed"] = compact(forms["tgv_ns_re1600_p4_32^3_mixed_noise"])
+        out["ns_mixed_ff"] = compact(forms["tgv_ns_re1600_p4_32^3_mixed_ff_noise"])
+        out["ns_fp64x"] = compact(forms["tgv_ns_re1600_p4_32^3_fp64x"])
+        out["euler_mixed"] = compact(forms["tgv_euler_p3_32^3_mixed"])
+        out["euler_mixed_ff"] = compact(forms["tgv_euler_p3_32^3_mixed_ff"])
+        out["euler_fp64x"] = compact(forms["tgv_euler_p3_32^3_fp64x"])
+        out["batch_fp64"] = compact(forms["batched_vortex_256_fp64"])
+        out["batch_mixed_ff"] = compact(forms["batched_vortex_256_mixed_ff"])
+    out["headline_volume_frac"] = {"of_unit_count_peak": round(achieved / peak, 3),
+                                   "of_measured_fma_peak": round(achieved / peak_meas, 3)}
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()
