@@ -107,10 +107,12 @@ def kernel_flops(p, n_el, stages=3):
     return {"prep": prep, "face": face, "relax": relax, "grad": grad}
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_volume launch of the
-# default workload, from the ncu capture summarised in profiles/ (stage 3 of a step, FP64).
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the k_volume launches of one
+# step of the default workload (stages 1, 2, 3; FP64, tile variant 1), from the ncu capture
+# summarised in profiles/; the roofline reports their mean, per launch like `achieved`.
 # It is reported only while the kernel sources hash to the value the capture was taken with.
-VOLUME_TRAFFIC = {"source_sha1": "de78239ba2e03a5495b6bae9234e18825dfd8dc8", "bytes_per_launch": 399555840 + 67871232}
+VOLUME_TRAFFIC = {"source_sha1": "f2ebd8c9296d6ec8a4a49b3480082c26ee9c435b",
+                  "bytes_per_stage": [147562240 + 50288384, 231834368 + 57167872, 399510784 + 67861504]}
 
 
 def kernel_source_sha1():
@@ -491,6 +493,48 @@ def measure_batch(precision, steps, warmup, count=256, ref_states=None, keep_sta
     return out
 
 
+def degree_rates(precision, steps=10, warmup=3, target_nodes=2_000_000):
+    """Relaxed-step throughput of one large isentropic-vortex instance per LGL degree
+    (p = 2..5, about target_nodes nodes each, the batch's box and vortex, tiles
+    autotuned): the rate each degree's kernels reach when the GPU is full of them."""
+    import torch
+    from paper_2003_08831_gb300 import inputs
+    from paper_2003_08831_gb300.solver import Solver, stable_dt
+    out = {}
+    for p in range(2, 6):
+        n = max(4, int(round((target_nodes / (p + 1) ** 3) ** (1.0 / 3.0))))
+        s = Solver(p, (n, n, n), (0.0,) * 3, (10.0,) * 3, precision=precision)
+        xyz = s.coords()
+        q0 = inputs.vortex_state(xyz[0], xyz[1], 0.0, eps=4.5, mach=0.3, centre=(5.0, 5.0), period=10.0)
+        dt = stable_dt(q0, p, [10.0 / n] * 3, 0.5)
+        q = s.to_device(q0)
+        s.autotune(q)
+        s.advance(q, warmup, dt, want_hist=False, want_gamma_elem=False)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        s.advance(q, steps, dt, want_hist=False, want_gamma_elem=False)
+        e1.record()
+        torch.cuda.synchronize()
+        out[p] = {"elements": n ** 3, "nodes": s.N, "value": s.N * STAGES * steps / (e0.elapsed_time(e1) / 1e3)}
+        s.close()
+    return out
+
+
+def degree_mix(form, params, precision):
+    """The batch against its degree mix: the rate predicted from the single-instance rate
+    of each degree (the batch's nodes of degree p take nodes_p / rate_p), and the
+    batch's measured rate as a fraction of that prediction."""
+    rates = degree_rates(precision)
+    nodes = {p: sum(d["n"] ** 3 * (p + 1) ** 3 for d in params if d["p"] == p) for p in range(2, 6)}
+    total = sum(nodes.values())
+    pred = total / sum(nodes[p] / rates[p]["value"] for p in nodes if nodes[p])
+    return {"single_instance_rate_per_degree": {str(p): rates[p]["value"] for p in rates},
+            "batch_nodes_per_degree": {str(p): nodes[p] for p in nodes},
+            "predicted_from_degree_mix": pred, "measured_over_predicted": form["value"] / pred}
+
+
 def measure_shock(precision, steps=50, warmup=3, n=25, p=3):
     """Section 4.1.2 form: the moving viscous shock on n^3 elements of [-0.5, 0.5]^3 (M 2.5,
     Re 10, Pr 3/4), Dirichlet-penalty boundaries on the x1 faces (exterior state evaluated on
@@ -702,6 +746,9 @@ def compact(form):
         out["speedup_vs_fp64"] = round(form["speedup_vs_fp64_same_physics"], 3)
     if "error_vs_fp64" in form:
         out["rel_l2_vs_fp64"] = form["error_vs_fp64"]["rel_l2"]
+    if "degree_mix" in form:
+        out["predicted_from_degree_mix"] = form["degree_mix"]["predicted_from_degree_mix"]
+        out["measured_over_predicted"] = round(form["degree_mix"]["measured_over_predicted"], 3)
     return out
 
 
@@ -759,10 +806,11 @@ def run_full(args, rank, world, local_rank):
         "gpu_launches": int(res["launches"]),
         "roofline": {"bound": "alu", "kernel": "k_volume (flux differencing + SATs)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": (VOLUME_TRAFFIC["bytes_per_launch"]
+                     "traffic": (sum(VOLUME_TRAFFIC["bytes_per_stage"]) / 3.0
                                  if VOLUME_TRAFFIC["source_sha1"] == kernel_source_sha1() and wl is WORKLOADS[MAIN]
                                  else None),
-                     "traffic_unit": "bytes per launch (ncu, same kernel sources)",
+                     "traffic_unit": "bytes per launch, mean of the step's three launches (ncu, same kernel "
+                                     "sources)",
                      "peak_source": "%s ALU peak from unit counts x median SM clock (%.0f MHz): 152 SMs x %s"
                                     % ("FP64" if wl["precision"] == 0 else "FP32", sm_mhz,
                                        "2 DFMA/clk" if wl["precision"] == 0 else "128 FFMA/clk"),
@@ -810,6 +858,10 @@ def run_full(args, rank, world, local_rank):
                            (2, "batched_vortex_256_fp64x")]:
             forms[name] = measure_batch(prec, 20, 3, ref_states=ref)
         del ref
+        from paper_2003_08831_gb300 import inputs as _inp
+        bparams = _inp.batch_instances(256)
+        for prec, name in [(0, "batched_vortex_256_fp64"), (3, "batched_vortex_256_mixed_ff")]:
+            forms[name]["degree_mix"] = degree_mix(forms[name], bparams, prec)
         fp = {"tgv_euler_p3_32^3_mixed": value, "tgv_euler_p3_32^3_mixed_ff": value,
               "tgv_euler_p3_32^3_fp64x": value,
               "tgv_ns_re1600_p4_32^3_fp64x": forms["tgv_ns_re1600_p4_32^3_fp64"]["value"],
