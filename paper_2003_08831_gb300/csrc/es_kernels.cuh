@@ -771,10 +771,23 @@ struct VolSmem {
 // line is evaluated here from the neighbours' face-node parameter vectors, with
 // k_face's arguments (the same bits on both elements of a face), instead of being read
 // from F: one launch less per stage and no face-flux round trip through global memory.
-template <int P1, typename TF, bool NS, int EPB, int THREADS, bool FACES = false>
-__global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const TF* __restrict__ aux,
-                                                   const TF* __restrict__ F, const TF* __restrict__ FL,
-                                                   const TF* __restrict__ fV) {
+// Register budget of the FP32 flux-differencing kernel, which waits on latency, not on its
+// FP32 pipe (measured on GB300, volume time per step, best tile): the Navier--Stokes form at
+// p = 4 runs 11-13 % faster at 85 registers than at its unbounded 106-121 (more warps per
+// SM), the Euler form at p = 5 7 % faster at 64; at p = 2, 3 a bound gives nothing or less.
+template <int P1, typename TF, bool NS>
+struct VolRegs {
+  static constexpr int cap = std::is_same<TF, float>::value ? (NS ? 80 : (P1 == 6 ? 64 : 0)) : 0;
+};
+template <int P1, typename TF, bool NS, int THREADS>
+constexpr int vol_min_blocks() {
+  return VolRegs<P1, TF, NS>::cap ? 65536 / (THREADS * VolRegs<P1, TF, NS>::cap) : 1;
+}
+
+template <int P1, typename TF, bool NS, int EPB, int THREADS, bool FACES>
+__device__ __forceinline__ void volume_body(const Params& P, const StageVol& sv, const TF* __restrict__ aux,
+                                            const TF* __restrict__ F, const TF* __restrict__ FL,
+                                            const TF* __restrict__ fV) {
   using S = VolSmem<P1, EPB, FACES>;
   constexpr int P2 = P1 * P1, Np = P1 * P2;
   constexpr int ZP = S::ZP;
@@ -1034,6 +1047,27 @@ __global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const
       if (doA) sv.A[e] = (sv.A_init ? 0.0 : sv.A[e]) + (wantA ? sv.A_scale * sA : 0.0);
     }
   }
+}
+
+// The kernel: the plain launch bound (the compiler's own register choice), or, where
+// VolRegs sets a cap, the minimum blocks per SM that enforce it (a minimum of one block
+// would change the compiler's choice for the uncapped kernels too).
+template <int P1, typename TF, bool NS, int EPB, int THREADS, bool FACES = false>
+__global__ void __launch_bounds__(THREADS) k_volume(Params P, StageVol sv, const TF* __restrict__ aux,
+                                                   const TF* __restrict__ F, const TF* __restrict__ FL,
+                                                   const TF* __restrict__ fV) {
+  volume_body<P1, TF, NS, EPB, THREADS, FACES>(P, sv, aux, F, FL, fV);
+}
+template <int P1, typename TF, bool NS, int EPB, int THREADS, bool FACES = false>
+__global__ void __launch_bounds__(THREADS, (vol_min_blocks<P1, TF, NS, THREADS>()))
+    k_volume_capped(Params P, StageVol sv, const TF* __restrict__ aux, const TF* __restrict__ F,
+                    const TF* __restrict__ FL, const TF* __restrict__ fV) {
+  volume_body<P1, TF, NS, EPB, THREADS, FACES>(P, sv, aux, F, FL, fV);
+}
+template <int P1, typename TF, bool NS, int EPB, int THREADS, bool FACES = false>
+constexpr auto vol_kernel() {
+  if constexpr (VolRegs<P1, TF, NS>::cap != 0) return k_volume_capped<P1, TF, NS, EPB, THREADS, FACES>;
+  else return k_volume<P1, TF, NS, EPB, THREADS, FACES>;
 }
 
 // ---------------------------------------------------------------------------
@@ -1630,9 +1664,9 @@ template <int P1, typename TF, int V>
 cudaError_t volume_setup_v() {
   using C = VolCfg<P1, V>;
   const int smem = (int)vol_smem_bytes<P1, C::EPB>(sizeof(TF));
-  cudaError_t e1 = cudaFuncSetAttribute(k_volume<P1, TF, false, C::EPB, C::THREADS>,
+  cudaError_t e1 = cudaFuncSetAttribute(vol_kernel<P1, TF, false, C::EPB, C::THREADS>(),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaError_t e2 = cudaFuncSetAttribute(k_volume<P1, TF, true, C::EPB, C::THREADS>,
+  cudaError_t e2 = cudaFuncSetAttribute(vol_kernel<P1, TF, true, C::EPB, C::THREADS>(),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e1 != cudaSuccess ? e1 : e2;
 }
@@ -1652,9 +1686,9 @@ void volume_v(const Params& P, const StageVol& sv, const TF* aux, const TF* F, c
   const int grid = (P.K + C::EPB - 1) / C::EPB;
   const size_t smem = vol_smem_bytes<P1, C::EPB>(sizeof(TF));
   if (ns)
-    k_volume<P1, TF, true, C::EPB, C::THREADS><<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, FL, fV);
+    vol_kernel<P1, TF, true, C::EPB, C::THREADS>()<<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, FL, fV);
   else
-    k_volume<P1, TF, false, C::EPB, C::THREADS><<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, FL, fV);
+    vol_kernel<P1, TF, false, C::EPB, C::THREADS>()<<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, FL, fV);
 }
 
 template <int P1, typename TF>
@@ -1672,7 +1706,7 @@ void Launcher<P1, TF>::volume(const Params& P, const StageVol& sv, const void* a
 template <int P1, int V>
 cudaError_t volface_setup_v() {
   using C = VolCfg<P1, V>;
-  return cudaFuncSetAttribute(k_volume<P1, float, false, C::EPB, C::THREADS, true>,
+  return cudaFuncSetAttribute(vol_kernel<P1, float, false, C::EPB, C::THREADS, true>(),
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)VolSmem<P1, C::EPB, true>::template bytes<float>());
 }
@@ -1692,7 +1726,7 @@ template <int P1, int V>
 void volface_v(const Params& P, const StageVol& sv, const float* aux, cudaStream_t st) {
   using C = VolCfg<P1, V>;
   const int grid = (P.K + C::EPB - 1) / C::EPB;
-  k_volume<P1, float, false, C::EPB, C::THREADS, true>
+  vol_kernel<P1, float, false, C::EPB, C::THREADS, true>()
       <<<grid, C::THREADS, VolSmem<P1, C::EPB, true>::template bytes<float>(), st>>>(P, sv, aux, nullptr, nullptr,
                                                                                      nullptr);
 }
