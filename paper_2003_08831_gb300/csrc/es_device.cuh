@@ -248,10 +248,11 @@ __device__ __forceinline__ void ec_flux(const Zstate<T>& a, const Zstate<T>& b, 
   const T mass = rho_hat * um;
   const T q2 = u0 * u0 + uy * uy + uz * uz;
   f[0] = mass;
-  f[1] = mass * u0;
-  f[2] = mass * uy;
-  f[3] = mass * uz;
-  f[1 + m] += p1;
+  // p1 joins the momentum flux of direction m inside one fma; constant indices keep f in
+  // registers (m is a run-time value)
+  f[1] = fma(mass, u0, m == 0 ? p1 : T(0));
+  f[2] = fma(mass, uy, m == 1 ? p1 : T(0));
+  f[3] = fma(mass, uz, m == 2 ? p1 : T(0));
   f[4] = um * p2g + (T(0.5) * mass) * q2;
 }
 
