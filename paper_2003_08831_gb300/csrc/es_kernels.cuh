@@ -481,7 +481,7 @@ __device__ __forceinline__ void matrix_dissipation(const Zstate<TF>& L, const Zs
   const TF a = C.sqrt_gam * iz1;
   const TF u2h = TF(0.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   const TF h = a * a * C.inv_gm1 + u2h;
-  const TF un = u[m];
+  const TF un = m == 0 ? u[0] : (m == 1 ? u[1] : u[2]);  // constant indices: u stays in registers
   const int t1 = m == 0 ? 1 : 0, t2 = m == 2 ? 1 : 2;
   // entropy-variable jump
   const TF ds = -(C.gam + TF(1)) * tf_log(R.z[0] * fast_rcp(L.z[0])) - C.gm1 * tf_log(R.z[4] * fast_rcp(L.z[4]));
@@ -980,17 +980,21 @@ __device__ __forceinline__ void volume_body(const Params& P, const StageVol& sv,
 #pragma unroll
       for (int v = 0; v < 5; ++v) kt[v] = acc[v * EPB * Np + t];
       if (sv.d_out) {
-        // d = dt (b_i k_i + sum_j b_j k_j): coefficients and dt split on the integer pipe
+        // d = dt (b_i k_i + sum_j b_j k_j): coefficients and dt split on the integer pipe;
+        // the earlier stages in order, each one's coefficient split once (no per-stage array)
         const ff dtf = ff_from_double(G.dt);
         const ff cs = ff_from_double(sv.dcoef_self);
-        ff cj[kMaxStages];  // one per earlier stage with b_j != 0 (sv.nd < kMaxStages)
-        for (int j = 0; j < sv.nd; ++j) cj[j] = ff_from_double(sv.dcoef[j]);
+        ff dv[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          ff dv = cs * to_ff(kt[v]);
-          for (int j = 0; j < sv.nd; ++j) ff_fma_acc(dv, cj[j], to_ff(static_cast<const TF*>(sv.dk[j])[v * N + g]));
-          sv.d_out[v * N + g] = double(ff_norm(dv) * dtf);
+        for (int v = 0; v < 5; ++v) dv[v] = cs * to_ff(kt[v]);
+        for (int j = 0; j < sv.nd; ++j) {
+          const ff cj = ff_from_double(sv.dcoef[j]);
+          const TF* dk = static_cast<const TF*>(sv.dk[j]);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) ff_fma_acc(dv[v], cj, to_ff(dk[v * N + g]));
         }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sv.d_out[v * N + g] = double(ff_norm(dv[v]) * dtf);
       } else if (sv.kout64) {
 #pragma unroll
         for (int v = 0; v < 5; ++v) sv.kout64[v * N + g] = double(kt[v]);
