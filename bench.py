@@ -111,8 +111,8 @@ def kernel_flops(p, n_el, stages=3):
 # step of the default workload (stages 1, 2, 3; FP64, tile variant 1), from the ncu capture
 # summarised in profiles/; the roofline reports their mean, per launch like `achieved`.
 # It is reported only while the kernel sources hash to the value the capture was taken with.
-VOLUME_TRAFFIC = {"source_sha1": "6777316223a3e663722ff7cc6e89f5c3a368154d",
-                  "bytes_per_stage": [147562240 + 50071808, 231703296 + 56825856, 399992576 + 67922432]}
+VOLUME_TRAFFIC = {"source_sha1": "00e0669677c6c78e2de3e00ae31026d8a601d23c",
+                  "bytes_per_stage": [147556096 + 49156096, 231833088 + 56261632, 399596544 + 65751296]}
 
 
 def kernel_source_sha1():
