@@ -58,3 +58,8 @@ def test_vortex_design_order(p, rk, diss):
     rate = np.polyfit(np.log2(10.0 / np.array(Ns)), np.log2(errs), 1)[0]
     print("p=%d diss=%d errors %s rate %.3f" % (p, diss, " ".join("%.3e" % e for e in errs), rate))
     assert rate > p + 0.5, (errs, rate)
+    if diss == 2:
+        # with the matrix dissipation the even degree comes within a quarter of design order
+        # (2.86 measured; the coarsest mesh, 16 elements over the vortex, is still
+        # under-resolved)
+        assert rate > p + 0.75, (errs, rate)
