@@ -275,6 +275,7 @@ struct Group {
   void* FL = nullptr;                    // -x_m boundary-face fluxes (tf bytes each)
   double* bcz = nullptr;                 // [3][2][kBcVals] exterior values at the stage time
   double* est = nullptr;                 // batch estimate step: eta_old, deta, eta_new [3][K]
+  int* nbr = nullptr;                    // [K][6] periodic neighbours (Params::nbr)
 };
 
 // The volume kernel with on-chip interface fluxes serves FP32 fluxes (ES_MIXED, ES_MIXED_FF)
@@ -456,6 +457,7 @@ void group_free(Group& g) {
   cudaFree(g.FL);
   cudaFree(g.bcz);
   cudaFree(g.est);
+  cudaFree(g.nbr);
   g = Group();
 }
 
@@ -558,6 +560,28 @@ int group_init(Group& g, const es_config* insts, int n, int stages, bool own_sta
     if (rc == ES_OK) rc = cuda_check(cudaMemcpy(g.elem_inst_dev, ei.data(), K * sizeof(int), cudaMemcpyHostToDevice));
     g.P.geom = g.geom_dev;
     g.P.elem_inst = g.elem_inst_dev;
+  }
+  if (rc == ES_OK) {  // periodic neighbour table: the kernels look neighbours up instead of dividing
+    std::vector<int> nb(size_t(K) * 6);
+    for (int i = 0; i < n; ++i) {
+      const InstGeom& G = g.geom[i];
+      const int dims[3] = {G.nx, G.ny, G.nz};
+      for (int ez = 0; ez < G.nz; ++ez)
+        for (int ey = 0; ey < G.ny; ++ey)
+          for (int ex = 0; ex < G.nx; ++ex) {
+            const int c[3] = {ex, ey, ez};
+            const long long e = G.off + ex + (long long)G.nx * (ey + (long long)G.ny * ez);
+            for (int m = 0; m < 3; ++m)
+              for (int side = 0; side < 2; ++side) {
+                int d[3] = {c[0], c[1], c[2]};
+                d[m] = (d[m] + (side ? 1 : -1) + dims[m]) % dims[m];
+                nb[e * 6 + m * 2 + side] = G.off + d[0] + G.nx * (d[1] + G.ny * d[2]);
+              }
+          }
+    }
+    rc = dev_alloc(&g.nbr, size_t(K) * 6);
+    if (rc == ES_OK) rc = cuda_check(cudaMemcpy(g.nbr, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice));
+    g.P.nbr = g.nbr;
   }
   if (rc == ES_OK) {  // gamma accumulators start at +inf, no update pending
     launch_reset(g.gmin, g.pending, n, nullptr);

@@ -76,6 +76,8 @@ struct Params {
   const int* elem_inst;        // device [K]: instance of each element (batches), or null
   int bc[3];                   // per direction: 0 periodic, 1 Dirichlet penalty (single instance)
   const double* bcz;           // device [3][2][kBcVals] exterior values (see kBcVals), or null
+  const int* nbr;              // device [K][6]: periodic neighbour of each element along -x_m, +x_m
+                               // (index 2 m + side), or null (then computed from the geometry)
 };
 
 template <typename T> __device__ __forceinline__ const FluxConst<T>& flux_const(const Params& P);
@@ -89,7 +91,11 @@ __device__ __forceinline__ int inst_of(const Params& P, int e) { return P.elem_i
 
 __device__ __forceinline__ const InstGeom& geom_of(const Params& P, int inst) { return P.geom ? P.geom[inst] : P.g0; }
 
+// Periodic neighbour of element e along direction m (dir = -1 or +1): from the context's
+// table when there is one (one cached load), else from the element's grid position (five
+// integer divisions).
 __device__ __forceinline__ int neighbour(const Params& P, int e, int m, int dir) {
+  if (P.nbr) return P.nbr[(long long)e * 6 + m * 2 + (dir > 0 ? 1 : 0)];
   const InstGeom& G = geom_of(P, inst_of(P, e));
   const int le = e - G.off;
   int ex = le % G.nx;

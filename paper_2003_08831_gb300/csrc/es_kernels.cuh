@@ -808,13 +808,15 @@ __device__ __forceinline__ void volume_body(const Params& P, const StageVol& sv,
     for (int c = 0; c < ZP; ++c) za[c * EPB * Np + t] = aux[c * N + (long long)e0 * Np + t];
   }
   if constexpr (FACES) {
-    // h = ((m * 2 + side) * nel + el) * P2 + ab: side 0 is the -x_m neighbour's last node
-    // on line (a, b), side 1 the +x_m neighbour's first
-    const int nh = 6 * nel * P2;
+    // h = ((m * 2 + side) * EPB + el) * P2 + ab: side 0 is the -x_m neighbour's last node
+    // on line (a, b), side 1 the +x_m neighbour's first (compile-time strides: no division
+    // by the ragged tile's element count)
+    constexpr int nh = 6 * EPB * P2;
     for (int h = threadIdx.x; h < nh; h += blockDim.x) {
       const int ab = h % P2;
       const int r = h / P2;
-      const int el = r % nel, ms = r / nel;
+      const int el = r % EPB, ms = r / EPB;
+      if (el >= nel) continue;
       const int m = ms >> 1, side = ms & 1;
       const int en = neighbour(P, e0 + el, m, side ? 1 : -1);
       const long long g = (long long)en * Np + line_node<P1>(m, ab % P1, ab / P1, side ? 0 : P1 - 1);
