@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -226,6 +227,25 @@ int grid_for_sms(int sm_count, long long n, int block) {
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
+}
+
+// double -> float-float with the device split's result (ff_from_double): in its fast
+// range (2^-74 <= |d| < 2^127, and zero) hi = d truncated to 24 significand bits and lo
+// the remainder rounded once; elsewhere hi = fl32(d), lo = fl32(d - hi)
+void ff_split_host(double d, float out[2]) {
+  uint64_t b;
+  std::memcpy(&b, &d, sizeof(b));
+  const unsigned e = unsigned(b >> 52) & 0x7FFu;
+  if (e - 949u < 202u || (b << 1) == 0) {
+    const uint64_t bt = b & ~((uint64_t(1) << 29) - 1);
+    double h;
+    std::memcpy(&h, &bt, sizeof(h));
+    out[0] = float(h);         // exact: 24 significand bits in range
+    out[1] = float(d - h);     // d - h exact; one rounding
+  } else {
+    out[0] = float(d);
+    out[1] = float(d - double(out[0]));
+  }
 }
 
 }  // namespace es
@@ -739,9 +759,11 @@ int group_step(Engine& E, Group& g, double* q, double* t, double* hist, cudaStre
     if (i == T.s - 1) {  // last stage: write d = dt sum_j b_j k_j instead of k_s
       sv.d_out = g.d;
       sv.dcoef_self = T.b[i];
+      ff_split_host(T.b[i], sv.dcoef_self_ff);
       for (int j = 0; j < i; ++j) {
         if (T.b[j] != 0.0) {
           sv.dcoef[sv.nd] = T.b[j];
+          ff_split_host(T.b[j], sv.dcoef_ff[sv.nd]);
           sv.dk[sv.nd] = g.k[j];
           sv.nd++;
         }

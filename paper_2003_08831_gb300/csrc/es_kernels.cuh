@@ -438,7 +438,7 @@ __global__ void k_prep(Params P, StagePrep sp, TF* __restrict__ aux, int* __rest
         ff dw[5];
         entropy_var_increment_ff(uf, ef, P.Cff, dw);
 #pragma unroll
-        for (int v = 0; v < 5; ++v) sp.dw[v * N + g] = double(dw[v]);
+        for (int v = 0; v < 5; ++v) reinterpret_cast<ff*>(sp.dw)[v * N + g] = dw[v];
       }
     }
   }
@@ -803,9 +803,26 @@ __device__ __forceinline__ void volume_body(const Params& P, const StageVol& sv,
   const FluxConst<TF> C = flux_const<TF>(P);
   const TF iw = tf_from_double<TF>(P.inv_omega_end);
 
-  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+  {
+    // all of this thread's loads issued before the first shared-memory store (compile-time
+    // trip count; the launch has THREADS threads)
+    constexpr int NT = (EPB * Np + THREADS - 1) / THREADS;
+    TF ld[NT][ZP];
+    const TF* __restrict__ src = aux + (long long)e0 * Np;
 #pragma unroll
-    for (int c = 0; c < ZP; ++c) za[c * EPB * Np + t] = aux[c * N + (long long)e0 * Np + t];
+    for (int i = 0; i < NT; ++i) {
+      const int t = threadIdx.x + i * THREADS;
+#pragma unroll
+      for (int c = 0; c < ZP; ++c)
+        if (t < nn) ld[i][c] = src[c * N + t];
+    }
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+      const int t = threadIdx.x + i * THREADS;
+#pragma unroll
+      for (int c = 0; c < ZP; ++c)
+        if (t < nn) za[c * EPB * Np + t] = ld[i][c];
+    }
   }
   if constexpr (FACES) {
     // h = ((m * 2 + side) * EPB + el) * P2 + ab: side 0 is the -x_m neighbour's last node
@@ -982,15 +999,15 @@ __device__ __forceinline__ void volume_body(const Params& P, const StageVol& sv,
 #pragma unroll
       for (int v = 0; v < 5; ++v) kt[v] = acc[v * EPB * Np + t];
       if (sv.d_out) {
-        // d = dt (b_i k_i + sum_j b_j k_j): coefficients and dt split on the integer pipe;
-        // the earlier stages in order, each one's coefficient split once (no per-stage array)
+        // d = dt (b_i k_i + sum_j b_j k_j): the coefficients split on the host, dt on the
+        // integer pipe; the earlier stages in order
         const ff dtf = ff_from_double(G.dt);
-        const ff cs = ff_from_double(sv.dcoef_self);
+        const ff cs(sv.dcoef_self_ff[0], sv.dcoef_self_ff[1]);
         ff dv[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) dv[v] = cs * to_ff(kt[v]);
         for (int j = 0; j < sv.nd; ++j) {
-          const ff cj = ff_from_double(sv.dcoef[j]);
+          const ff cj(sv.dcoef_ff[j][0], sv.dcoef_ff[j][1]);
           const TF* dk = static_cast<const TF*>(sv.dk[j]);
 #pragma unroll
           for (int v = 0; v < 5; ++v) ff_fma_acc(dv[v], cj, to_ff(dk[v * N + g]));
@@ -1020,7 +1037,7 @@ __device__ __forceinline__ void volume_body(const Params& P, const StageVol& sv,
         // omega_i omega_j omega_k w-increment . k in float-float; J dt enter per element
         ff sum(0.0f, 0.0f);
 #pragma unroll
-        for (int v = 0; v < 5; ++v) ff_fma_acc(sum, ff_from_double(sv.dw[v * N + g]), to_ff(kt[v]));
+        for (int v = 0; v < 5; ++v) ff_fma_acc(sum, reinterpret_cast<const ff*>(sv.dw)[v * N + g], to_ff(kt[v]));
         reinterpret_cast<ff*>(red)[EPB * Np + t] = mass_weight_ff<P1>(P, n) * ff_norm(sum);
       }
     }

@@ -13,6 +13,7 @@ int validate_config(const es_config& C);
 InstGeom instance_geom(const es_config& C, int off);
 void build_params(const es_config& C, Params* out);
 int grid_for_sms(int sm_count, long long n, int block);
+void ff_split_host(double d, float out[2]);
 
 // explicit Runge--Kutta tableaux of up to kMaxStages stages
 constexpr int kMaxStages = 10;
@@ -26,7 +27,8 @@ struct StagePrep {
   int nprev;
   double coef[kMaxStages];  // a_ij (multiplied by the instance's dt in the kernel)
   const void* k[kMaxStages];  // stage values in the flux precision (double, float or float-float)
-  double* dw;               // w(y) - w(u) output, or nullptr
+  double* dw;               // w(y) - w(u) output, or nullptr (FP64; float-float estimate
+                            // modes store (hi, lo) float pairs in the same 8 bytes)
   int Np;
 };
 
@@ -39,8 +41,13 @@ struct StageVol {
   double dcoef[kMaxStages];    // b_j
   const void* dk[kMaxStages];  // earlier stages' k in the flux precision
   double dcoef_self;   // b_i
+  // the same coefficients as float-float pairs (hi, lo), split on the host exactly as
+  // ff_from_double splits on the device (float-float estimate modes read these)
+  float dcoef_ff[kMaxStages][2];
+  float dcoef_self_ff[2];
   double* E;           // (eta' f)(y^i) per element, or nullptr
-  const double* dw;    // w(y^i) - w(u), or nullptr
+  const double* dw;    // w(y^i) - w(u), or nullptr (float-float estimate modes: (hi, lo)
+                       // float pairs in the same 8 bytes per value)
   double* A;           // relaxation term accumulator, or nullptr
   double A_scale;      // -b_i (times the instance's dt in the kernel)
   int A_init;          // first stage of the step: A starts at zero
