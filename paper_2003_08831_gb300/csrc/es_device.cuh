@@ -202,7 +202,14 @@ __device__ __forceinline__ double fast_rcp(double x) {
   const double e = fma(-x, r, 1.0);
   return fma(r, fma(e, e, e), r);
 }
-__device__ __forceinline__ float fast_rcp(float x) { return 1.0f / x; }
+// FP32 (the mixed modes' fluxes): the hardware approximation refined by one Newton step
+// r + r (1 - x r), within about an ulp of 1/x, without the IEEE division's special-case
+// path (x is a normal nonzero product of parameter-vector sums)
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return __fmaf_rn(r, __fmaf_rn(-x, r, 1.0f), r);
+}
 __device__ __forceinline__ ff fast_rcp(ff x) { return ff_rcp(x); }
 
 // |z| <= t for a positive threshold t, on the integer pipe (sign bit cleared)

@@ -1678,15 +1678,11 @@ void Launcher<P1, TF>::grad(const Params& P, const void* aux, void* fV, cudaStre
                                                                       static_cast<TF*>(fV));
 }
 
-template <int P1, int EPB>
-constexpr size_t vol_smem_bytes(size_t tf) {
-  return size_t(EPB) * P1 * P1 * P1 * ((kAux + 5) * tf + 2 * sizeof(double));  // VolSmem<P1, EPB, false>
-}
 
 template <int P1, typename TF, int V>
 cudaError_t volume_setup_v() {
   using C = VolCfg<P1, V>;
-  const int smem = (int)vol_smem_bytes<P1, C::EPB>(sizeof(TF));
+  const int smem = (int)VolSmem<P1, C::EPB, false>::template bytes<TF>();
   cudaError_t e1 = cudaFuncSetAttribute(vol_kernel<P1, TF, false, C::EPB, C::THREADS>(),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaError_t e2 = cudaFuncSetAttribute(vol_kernel<P1, TF, true, C::EPB, C::THREADS>(),
@@ -1707,7 +1703,7 @@ void volume_v(const Params& P, const StageVol& sv, const TF* aux, const TF* F, c
               cudaStream_t st) {
   using C = VolCfg<P1, V>;
   const int grid = (P.K + C::EPB - 1) / C::EPB;
-  const size_t smem = vol_smem_bytes<P1, C::EPB>(sizeof(TF));
+  const size_t smem = VolSmem<P1, C::EPB, false>::template bytes<TF>();
   if (ns)
     vol_kernel<P1, TF, true, C::EPB, C::THREADS>()<<<grid, C::THREADS, smem, st>>>(P, sv, aux, F, FL, fV);
   else
