@@ -98,6 +98,10 @@ __device__ __forceinline__ ff ff_twice(ff x) { return ff(2.0f * x.hi, 2.0f * x.l
 // log(1 + z) - z for |z| <= 1e-3: z^2 (-1/2 + z/3 + tail) with z^2, z/3 and the sum in
 // float-float and the tail -z^2/4 + z^3/5 - z^4/6 + z^5/7 (below 5e-7 of the 1/2) in
 // FP32, so the result carries ~2^-47 relative error; larger |z| through FP64.
+// the rare wide-argument branch out of line: the float-float solve and stage preparation
+// inline ff_log1pmx at every call site, and an inlined FP64 fallback at each of them
+// costs instruction-cache space in the hot loops
+static __device__ __noinline__ ff ff_log1pmx_wide(ff z) { return ff(log1pmx(double(z))); }
 __device__ __forceinline__ ff ff_log1pmx(ff z) {
   if (fabsf(z.hi) <= 1e-3f) {
     const float t = z.hi;
@@ -115,7 +119,7 @@ __device__ __forceinline__ ff ff_log1pmx(ff z) {
     const ff poly = fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(ez, tail)));
     return (z * z) * poly;
   }
-  return ff(log1pmx(double(z)));
+  return ff_log1pmx_wide(z);
 }
 
 // 1/sqrt(x): the FP32 approximation r (rsqrt.approx.ftz.f32, ~2^-23) refined with the
