@@ -6,7 +6,8 @@ Setup: entropy-stable (Rusanov) interfaces, a 2D vortex extruded over one elemen
 in x3, periodic box [-5, 5]^2, t_end = 1, CFL 0.5 (the time step shrinks with h),
 N = 16, 32, 64 elements per direction (h = 0.625 to 0.156; Table 1 spans h = 1 to
 0.125).  The paper pairs p = 2 with BSRK(4,3) and p = 3 with RK(4,4) (Table 1) and
-observes L2 density rates of 3.2 and 4.5; this setup (3-stage BS3 for p = 2) gives
+observes L2 density rates of 3.2 and 4.5; this setup (BS3, which advances as BSRK(4,3) with
+fixed steps: its fourth stage feeds only the embedded pair) gives
 2.6 and 4.0 with Rusanov interfaces and 2.9 for p = 2 with the matrix interface
 dissipation (interface_diss = 2).
 """
