@@ -53,32 +53,37 @@ template <> struct VolCfg<6, 2> { static constexpr int EPB = 8, THREADS = 288; }
 // dw1 = -ds/(gam-1) - beta[(x-y)|v|^2 + (1+x)(2 v.dv + |dv|^2)]/(2(1+y)),
 // dw_v = beta[(x-y) v + (1+x) dv]/(1+y), dw5 = -beta (x-y)/(1+y).
 // With Pr = rho p = (gam-1)(rho E - |m|^2/2), one division 1/(rho rho' Pr) gives
-// 1/rho, 1/rho' and 1/p; a second gives 1/(1+y).
+// 1/rho, 1/rho' and 1/p (|v|^2 = |m|^2/rho^2); a second gives beta/(1+y), shared by
+// every component.
 __device__ __forceinline__ void entropy_var_increment(const double u[5], const double e[5], double gam,
                                                       double inv_gm1, double dw[5]) {
+  const double gm1 = gam - 1.0;
   const double rho = u[0];
   const double rho1 = rho + e[0];
   const double m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
-  const double Pr = (gam - 1.0) * (rho * u[4] - 0.5 * m2);
-  const double inv = fast_rcp(rho * rho1 * Pr);
-  const double ir = rho1 * Pr * inv, ir1 = rho * Pr * inv, ip = rho * rho * rho1 * inv;
+  const double Pr = gm1 * (rho * u[4] - 0.5 * m2);
+  const double rr1 = rho * rho1;
+  const double inv = fast_rcp(rr1 * Pr);
+  const double pinv = Pr * inv;
+  const double ir = rho1 * pinv, ir1 = rho * pinv, ip = rho * rr1 * inv;
   const double v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
-  const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
+  const double v2s = m2 * ir * ir;
   const double x = e[0] * ir;
   const double d0 = (e[1] - v0 * e[0]) * ir1, d1 = (e[2] - v1 * e[0]) * ir1, d2 = (e[3] - v2 * e[0]) * ir1;
   const double dv2 = d0 * d0 + d1 * d1 + d2 * d2;
   const double y =
-      (gam - 1.0) * (e[4] - (v0 * e[1] + v1 * e[2] + v2 * e[3]) + 0.5 * v2s * e[0] - 0.5 * rho1 * dv2) * ip;
+      gm1 * (e[4] - (v0 * e[1] + v1 * e[2] + v2 * e[3]) + 0.5 * v2s * e[0] - 0.5 * rho1 * dv2) * ip;
   const double beta = rho * ip;
-  const double iy = fast_rcp(1.0 + y);
+  const double biy = beta * fast_rcp(1.0 + y);  // beta / (1 + y)
   const double ds = (y + log1pmx(y)) - gam * (x + log1pmx(x));
   const double xy = x - y;
-  const double dkin = 0.5 * beta * (xy * v2s + (1.0 + x) * (2.0 * (v0 * d0 + v1 * d1 + v2 * d2) + dv2)) * iy;
+  const double opx = 1.0 + x;
+  const double dkin = 0.5 * biy * (xy * v2s + opx * (2.0 * (v0 * d0 + v1 * d1 + v2 * d2) + dv2));
   dw[0] = -ds * inv_gm1 - dkin;
-  dw[1] = beta * (xy * v0 + (1.0 + x) * d0) * iy;
-  dw[2] = beta * (xy * v1 + (1.0 + x) * d1) * iy;
-  dw[3] = beta * (xy * v2 + (1.0 + x) * d2) * iy;
-  dw[4] = -beta * xy * iy;
+  dw[1] = biy * (xy * v0 + opx * d0);
+  dw[2] = biy * (xy * v1 + opx * d1);
+  dw[3] = biy * (xy * v2 + opx * d2);
+  dw[4] = -biy * xy;
 }
 
 // ---------------------------------------------------------------------------
@@ -147,25 +152,26 @@ __device__ __forceinline__ void entropy_var_increment_ff(const ff u[5], const ff
   const ff rho1 = rho + e[0];
   const ff m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
   const ff Pr = C.gm1 * (rho * u[4] - ff_half(m2));
-  const ff inv = ff_rcp(rho * rho1 * Pr);
-  const ff ir = rho1 * Pr * inv, ir1 = rho * Pr * inv, ip = rho * rho * rho1 * inv;
+  const ff rr1 = rho * rho1;
+  const ff inv = ff_rcp(rr1 * Pr);
+  const ff pinv = Pr * inv;
+  const ff ir = rho1 * pinv, ir1 = rho * pinv, ip = rho * rr1 * inv;
   const ff v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
-  const ff v2s = v0 * v0 + v1 * v1 + v2 * v2;
+  const ff v2s = m2 * ir * ir;
   const ff x = e[0] * ir;
   const ff d0 = (e[1] - v0 * e[0]) * ir1, d1 = (e[2] - v1 * e[0]) * ir1, d2 = (e[3] - v2 * e[0]) * ir1;
   const ff dv2 = d0 * d0 + d1 * d1 + d2 * d2;
   const ff y = C.gm1 * (e[4] - (v0 * e[1] + v1 * e[2] + v2 * e[3]) + ff_half(v2s * e[0]) - ff_half(rho1 * dv2)) * ip;
-  const ff beta = rho * ip;
-  const ff iy = ff_rcp(one + y);
+  const ff biy = (rho * ip) * ff_rcp(one + y);  // beta / (1 + y)
   const ff ds = (y + ff_log1pmx(y)) - C.gam * (x + ff_log1pmx(x));
   const ff xy = x - y;
   const ff opx = one + x;
-  const ff dkin = ff_half(beta * (xy * v2s + opx * (ff_twice(v0 * d0 + v1 * d1 + v2 * d2) + dv2)) * iy);
+  const ff dkin = ff_half(biy * (xy * v2s + opx * (ff_twice(v0 * d0 + v1 * d1 + v2 * d2) + dv2)));
   dw[0] = -(ds * C.inv_gm1) - dkin;
-  dw[1] = beta * (xy * v0 + opx * d0) * iy;
-  dw[2] = beta * (xy * v1 + opx * d1) * iy;
-  dw[3] = beta * (xy * v2 + opx * d2) * iy;
-  dw[4] = -(beta * xy * iy);
+  dw[1] = biy * (xy * v0 + opx * d0);
+  dw[2] = biy * (xy * v1 + opx * d1);
+  dw[3] = biy * (xy * v2 + opx * d2);
+  dw[4] = -(biy * xy);
 }
 
 // Lanes per element in the relaxation kernels: a group of SUB lanes solves one element,
@@ -313,9 +319,11 @@ __device__ __forceinline__ void stage_increment_f64(const Params& P, const Stage
 }
 template <typename TF>
 __device__ __forceinline__ bool stage_z_f64(const Params& P, const double u[5], const double e[5], TF z[6]) {
+  // y = u + e formed in float-float on the FP32 pipe (the FP64 pipe bounds this kernel):
+  // the parameter vector is rounded to FP32 in the end either way
   ff yf[5], zf[6];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) yf[v] = ff_from_double(u[v] + e[v]);
+  for (int v = 0; v < 5; ++v) yf[v] = ff_from_double(u[v]) + ff_from_double(e[v]);
   const bool ok = param_vector_ff(yf, P.Cff, zf);
 #pragma unroll
   for (int c = 0; c < 6; ++c) z[c] = tf_from_ff<TF>(zf[c]);
