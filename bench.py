@@ -111,8 +111,8 @@ def kernel_flops(p, n_el, stages=3):
 # step of the default workload (stages 1, 2, 3; FP64, tile variant 1), from the ncu capture
 # summarised in profiles/; the roofline reports their mean, per launch like `achieved`.
 # It is reported only while the kernel sources hash to the value the capture was taken with.
-VOLUME_TRAFFIC = {"source_sha1": "809cff22ca0b86f56a52155e4e78286c245667e3",
-                  "bytes_per_stage": [148729088 + 48804864, 232502272 + 56104448, 400358912 + 65686272]}
+VOLUME_TRAFFIC = {"source_sha1": "c5545bb4b942e0fb822da311e48ba80a1e973060",
+                  "bytes_per_stage": [148372224 + 48975872, 232935424 + 56031232, 400283392 + 65723648]}
 
 
 def kernel_source_sha1():
