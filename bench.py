@@ -84,35 +84,24 @@ def volume_flops_per_element(p, ns=False, with_A=False):
 #   states from z 2 x 19, lambda 2, 5 jump terms 15);
 # k_prep per node: parameter vector 22 + 10 per earlier stage combined (+10 for the pending
 #   update in the first stage); entropy-variable increments 131 in stages 2 and 3;
-# k_relax per node and step: setup 85 (primitive state 35, X0 Y0 V2 25, a and the cubic
-#   coefficient 25) + 75 per Bregman evaluation (one for a smooth step from the cubic start).
+# k_relax per node and step: setup 65 in the solve's arithmetic (primitive state 35, X0 Y0 V2
+#   25, a 5) and the cubic starting coefficient 20, which both solves take in FP32, + 75 per
+#   Bregman evaluation (one for a smooth step from the cubic start).
 # k_grad per node (Navier--Stokes): entropy variables from z 4; per direction the D product
 #   8 (p+1), the metric 4 and the face lifting 12 on the 2/(p+1) face nodes; chain rule 90
 #   (velocity 3, 1/w_5 1, velocity gradients 27, temperature gradients 9, divergence 2,
 #   stresses 27, energy fluxes 21).
 FACE_FLOPS_PER_FACE_NODE = 56 + 55
 PREP_FLOPS_Z, PREP_FLOPS_PER_STAGE, PREP_FLOPS_PENDING, PREP_FLOPS_DW = 22, 10, 10, 131
-RELAX_FLOPS_SETUP, RELAX_FLOPS_EVAL = 85, 75
-
-
-def kernel_flops(p, n_el, stages=3):
-    """Algorithmic FP64 flops per launch (averaged over the step's launches) of each kernel."""
-    P1 = p + 1
-    nodes = n_el * P1 ** 3
-    prep = nodes * (PREP_FLOPS_Z * stages + PREP_FLOPS_PENDING
-                    + sum(PREP_FLOPS_PER_STAGE * i + (PREP_FLOPS_DW if i > 0 else 0) for i in range(stages))) / stages
-    face = 3 * n_el * P1 * P1 * FACE_FLOPS_PER_FACE_NODE
-    relax = nodes * (RELAX_FLOPS_SETUP + RELAX_FLOPS_EVAL)
-    grad = nodes * (4 + 3 * (8 * P1 + 4 + 24.0 / P1) + 90)
-    return {"prep": prep, "face": face, "relax": relax, "grad": grad}
+RELAX_FLOPS_SETUP, RELAX_FLOPS_CUBIC, RELAX_FLOPS_EVAL = 65, 20, 75
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the k_volume launches of one
 # step of the default workload (stages 1, 2, 3; FP64, tile variant 1), from the ncu capture
 # summarised in profiles/; the roofline reports their mean, per launch like `achieved`.
 # It is reported only while the kernel sources hash to the value the capture was taken with.
-VOLUME_TRAFFIC = {"source_sha1": "c5545bb4b942e0fb822da311e48ba80a1e973060",
-                  "bytes_per_stage": [148372224 + 48975872, 232935424 + 56031232, 400283392 + 65723648]}
+VOLUME_TRAFFIC = {"source_sha1": "9ead7ce83383f973f27e285f991389a131516fd2",
+                  "bytes_per_stage": [148340480 + 48874752, 232487680 + 55985664, 400438528 + 65617408]}
 
 
 def kernel_source_sha1():
@@ -213,7 +202,8 @@ def kernel_work(p, n_el, precision, ns=False, stages=3):
             b += 12 * tf * nodes
         by += b
     out["volume"] = ({k: v / stages for k, v in fl.items()}, by / stages)
-    out["relax"] = ({ar["relax"]: nodes * (RELAX_FLOPS_SETUP + RELAX_FLOPS_EVAL)}, 80.0 * nodes)
+    out["relax"] = ({ar["relax"]: nodes * (RELAX_FLOPS_SETUP + RELAX_FLOPS_EVAL), "f32": nodes * RELAX_FLOPS_CUBIC},
+                    80.0 * nodes)
     if ns:
         out["grad"] = ({ar["flux"]: nodes * (4 + 3 * (8 * P1 + 4 + 24.0 / P1) + 90)}, nodes * (5 + 12) * tf)
     return out
@@ -569,24 +559,6 @@ def measure_shock(precision, steps=50, warmup=3, n=25, p=3):
             "elements": n ** 3, "p": p, "rk": "RK(4,4) (4 stages)", "boundaries": "Dirichlet penalty on x1 (exact solution)",
             "t_end": t.item(), "density_rel_l2_error_vs_exact": float(np.linalg.norm(err) / np.linalg.norm(
                 inputs.viscous_shock_state(xyz[0], t.item(), prm)[0]))}
-
-
-def kernel_roofline(p, n_el, wl, prof, peak, vol_flops):
-    """Per kernel kind: algorithmic flops per launch / average event-timed launch, as a
-    fraction of the ALU peak (FP64 workloads; other precisions report null)."""
-    if wl["precision"] != 0:
-        return None
-    fl = kernel_flops(p, n_el)
-    if wl["mu"] == 0.0:
-        del fl["grad"]
-    fl["volume"] = vol_flops
-    out = {}
-    for k, f in fl.items():
-        ms, n = prof.get(k, (0.0, 0))
-        if n:
-            a = f / (ms / n * 1e-3) / 1e12
-            out[k] = {"flops_per_launch": f, "avg_launch_ms": ms / n, "achieved_tflops": a, "frac": a / peak}
-    return out
 
 
 def kernel_profile(res, steps):

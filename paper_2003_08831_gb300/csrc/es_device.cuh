@@ -457,18 +457,6 @@ __device__ __forceinline__ bool relax_node_eval(const RelaxNode& nd, double g, d
   return true;
 }
 
-// g^3 coefficient of D_n(g)/rho_n: with y2 = -(gam-1) V2/2 and L2 = y2 - Y0^2/2 (the g^2
-// coefficient of log1p(y)),
-//   D_3 = [-gam X0^3/6 + (2 Y0 L2 + y2 Y0)/3 - X0 L2]/(gam-1) - X0 V2/2;
-// the g^2 coefficient is D_2 = [(gam-1) X0^2 + (X0 - Y0)^2]/(2 (gam-1)) + V2/2.
-__device__ __forceinline__ double relax_node_cubic(const RelaxNode& nd, double gam, double inv_gm1) {
-  const double X = nd.X0, Y = nd.Y0;
-  const double y2 = -0.5 * (gam - 1.0) * nd.V2;
-  const double L2 = fma(-0.5 * Y, Y, y2);
-  const double t = (2.0 * Y * L2 + y2 * Y) * (1.0 / 3.0) - gam * X * X * X * (1.0 / 6.0) - X * L2;
-  return t * inv_gm1 - 0.5 * X * nd.V2;
-}
-
 // ---------------------------------------------------------------------------
 // warp reductions (butterfly: every lane ends with the same sum/min)
 __device__ __forceinline__ double warp_sum(double v) {

@@ -228,8 +228,12 @@ __device__ __forceinline__ void relax_node_setup_ff(const ff u[5], const ff d[5]
   nd.c = c;
 }
 
-// the g^3 coefficient (relax_node_cubic) in FP32: it only sets the starting point, whose
-// last bits still decide where Newton's iterates stop, so every operation is an explicit
+// g^3 coefficient of D_n(g)/rho_n: with y2 = -(gam-1) V2/2 and L2 = y2 - Y0^2/2 (the g^2
+// coefficient of log1p(y)),
+//   D_3 = [-gam X0^3/6 + (2 Y0 L2 + y2 Y0)/3 - X0 L2]/(gam-1) - X0 V2/2;
+// the g^2 coefficient is D_2 = [(gam-1) X0^2 + (X0 - Y0)^2]/(2 (gam-1)) + V2/2.
+// Taken in FP32 by both relaxation solves: it only sets the starting point, whose last
+// bits still decide where Newton's iterates stop, so every operation is an explicit
 // round-to-nearest one (the compiler may then not fuse them differently from one build
 // or register budget to the next)
 __device__ __forceinline__ float relax_node_cubic_f(const RelaxNodeF& nd, float gam) {
@@ -1111,7 +1115,7 @@ constexpr auto vol_kernel() {
 // V2 = rho |dv|^2/p, c = P_n rho.  r(g) = sum_n c D_n(g)/rho_n + g A,
 // r'(g) = sum_n c dD_n/dg + A; a = r''(0)/2 = sum c (X0^2 + (X0-Y0)^2/(gam-1) + V2)/2.
 // Newton from the root of the cubic model a g^2 + b g^3 + A g (b from
-// relax_node_cubic), safeguarded by the bracket [lo, hi] (r(lo) <= 0 < r(hi)); r is
+// relax_node_cubic_f, FP32), safeguarded by the bracket [lo, hi] (r(lo) <= 0 < r(hi)); r is
 // convex, so Newton converges from above.
 // Near the root the error after a step s is ~ s^2 r''/(2 r') ~ s^2/g, so a step
 // |s| <= root_rtol g (default 1e-8) leaves an error ~1e-16 g: the updated iterate is
@@ -1123,6 +1127,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
   const long long N = (long long)P.K * Np;
   const double gam = P.gam;
   const double inv_gm1 = P.Cd.inv_gm1;
+  const float gamf = tf_from_double<float>(gam);
   const int lane = threadIdx.x & 31;
   const int sl = lane % SUB;                  // lane within the element's group
   const unsigned gmask = RG::mask(lane);
@@ -1132,7 +1137,8 @@ __global__ void k_relax(Params P, StageRelax sr) {
     const int inst = inst_of(P, e);
     const double J = geom_of(P, inst).J;
     RelaxNode nd[R];
-    double a_part = 0.0, s_part = 0.0, A_part = 0.0, b_part = 0.0;
+    double a_part = 0.0, s_part = 0.0, A_part = 0.0;
+    float b_part = 0.0f;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = sl + SUB * r;
@@ -1160,7 +1166,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
         const double inv = fast_rcp(rho * Pr);
         const double ir = Pr * inv, ip = rho * rho * inv;
         const double v0 = u[1] * ir, v1 = u[2] * ir, v2 = u[3] * ir;
-        const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
+        const double v2s = m2 * ir * ir;
         const double dv0 = (d[1] - v0 * d[0]) * ir, dv1 = (d[2] - v1 * d[0]) * ir, dv2 = (d[3] - v2 * d[0]) * ir;
         const double Pn = mass_weight<P1>(P, J, n);
         nd[r].X0 = d[0] * ir;
@@ -1170,7 +1176,11 @@ __global__ void k_relax(Params P, StageRelax sr) {
         const double XY = nd[r].X0 - nd[r].Y0;
         a_part += 0.5 * nd[r].c * (nd[r].X0 * nd[r].X0 + XY * XY * inv_gm1 + nd[r].V2);
         s_part += nd[r].c;
-        b_part += nd[r].c * relax_node_cubic(nd[r], gam, inv_gm1);
+        // the starting point's cubic term in FP32, from the node values rounded on the
+        // integer pipe (the FP64 pipe bounds this kernel)
+        const RelaxNodeF nf{ff(tf_from_double<float>(nd[r].X0), 0.0f), ff(tf_from_double<float>(nd[r].Y0), 0.0f),
+                            ff(tf_from_double<float>(nd[r].V2), 0.0f), ff(0.0f, 0.0f)};
+        b_part = __fmaf_rn(tf_from_double<float>(nd[r].c), relax_node_cubic_f(nf, gamf), b_part);
         if (sr.u_new) {
           // A = sum P w(u).d - d_eta with w = ((gam - s)/(gam-1) - beta|v|^2/2, beta v, -beta)
           const double beta = rho * ip;
@@ -1184,7 +1194,7 @@ __global__ void k_relax(Params P, StageRelax sr) {
     const double a = group_sum<SUB>(a_part, gmask);
     const double ssum = group_sum<SUB>(s_part, gmask);
     // the cubic coefficient only moves the starting point: an FP32 sum
-    const double bcub = group_sum_f<SUB>(float(b_part), gmask);
+    const double bcub = group_sum_f<SUB>(b_part, gmask);
     double A;
     if (sr.u_new) A = group_sum<SUB>(A_part, gmask) - sr.deta[e];
     else A = sr.A[e];

@@ -40,12 +40,13 @@ def test_roofline_model_bytes_flops_and_bound():
     # k_face: 3 K P2 face-node pairs, 17 flux-precision values each
     assert w["face"][1] == 3 * K * P2 * 17 * 8
     assert w["face"][0] == {"f64": 3 * K * P2 * 111}
-    # k_relax: u and d (80 B per node)
+    # k_relax: u and d (80 B per node); the cubic starting coefficient on the FP32 pipe
     assert w["relax"][1] == 80 * nodes
+    assert w["relax"][0] == pytest.approx({"f64": nodes * (65 + 75), "f32": nodes * 20})
     # mixed modes: the flux in FP32, the estimate parts in FP64 (ES_MIXED) or float-float
     wm, wf = bench.kernel_work(p, K, precision=1), bench.kernel_work(p, K, precision=3)
-    assert set(wm["face"][0]) == {"f32"} and set(wm["relax"][0]) == {"f64"}
-    assert set(wf["relax"][0]) == {"ff"} and wf["face"][1] == 3 * K * P2 * 17 * 4
+    assert set(wm["face"][0]) == {"f32"} and set(wm["relax"][0]) == {"f64", "f32"}
+    assert set(wf["relax"][0]) == {"ff", "f32"} and wf["face"][1] == 3 * K * P2 * 17 * 4
     # bound and fraction: a 1 ms launch of k_face at 1 TFLOP/s FP64 needs
     # 3 K P2 111 / 1e12 s of the FP64 pipe; with that the larger roofline time
     peaks = {"fp64_tflops": 1.0, "fp32_tflops": 64.0}
@@ -57,5 +58,5 @@ def test_roofline_model_bytes_flops_and_bound():
     assert r["face"]["frac"] == pytest.approx(max(r["face"]["frac_fp64"], r["face"]["frac_hbm"]))
     # float-float work occupies the FP32 pipe at 2 x FF_INSTR_PER_OP flops per operation
     rf = bench.kernel_rooflines(p, K, 3, prof, peaks)
-    ff = bench.kernel_work(p, K, precision=3)["relax"][0]["ff"]
-    assert rf["relax"]["frac_fp32"] == pytest.approx(2 * bench.FF_INSTR_PER_OP * ff / 64e12 / 1e-3)
+    wr = bench.kernel_work(p, K, precision=3)["relax"][0]
+    assert rf["relax"]["frac_fp32"] == pytest.approx((wr["f32"] + 2 * bench.FF_INSTR_PER_OP * wr["ff"]) / 64e12 / 1e-3)
