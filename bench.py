@@ -83,7 +83,8 @@ def volume_flops_per_element(p, ns=False, with_A=False):
 # k_face per face node: Ismail--Roe flux 56 + Rusanov dissipation 55 (two conserved
 #   states from z 2 x 19, lambda 2, 5 jump terms 15);
 # k_prep per node: parameter vector 22 + 10 per earlier stage combined (+10 for the pending
-#   update in the first stage); entropy-variable increments 131 in stages 2 and 3;
+#   update in the first stage); entropy-variable increments 122 in stages 2 and 3 (one
+#   division for 1/rho, 1/rho', 1/p and one for beta/(1+y), log1p(z) - z counted as 1);
 # k_relax per node and step: setup 65 in the solve's arithmetic (primitive state 35, X0 Y0 V2
 #   25, a 5) and the cubic starting coefficient 20, which both solves take in FP32, + 75 per
 #   Bregman evaluation (one for a smooth step from the cubic start).
@@ -92,7 +93,7 @@ def volume_flops_per_element(p, ns=False, with_A=False):
 #   (velocity 3, 1/w_5 1, velocity gradients 27, temperature gradients 9, divergence 2,
 #   stresses 27, energy fluxes 21).
 FACE_FLOPS_PER_FACE_NODE = 56 + 55
-PREP_FLOPS_Z, PREP_FLOPS_PER_STAGE, PREP_FLOPS_PENDING, PREP_FLOPS_DW = 22, 10, 10, 131
+PREP_FLOPS_Z, PREP_FLOPS_PER_STAGE, PREP_FLOPS_PENDING, PREP_FLOPS_DW = 22, 10, 10, 122
 RELAX_FLOPS_SETUP, RELAX_FLOPS_CUBIC, RELAX_FLOPS_EVAL = 65, 20, 75
 
 

@@ -35,7 +35,7 @@ def test_roofline_model_bytes_flops_and_bound():
     # the parameter vector and the entropy increments (48 + 40)
     prep_bytes = nodes * ((40 + 80 + 48) + 2 * (40 + 40 + 48 + 40)) / 3
     assert w["prep"][1] == pytest.approx(prep_bytes)
-    prep_flops = nodes * (3 * 22 + 10 + (10 + 131) * 2) / 3
+    prep_flops = nodes * (3 * 22 + 10 + (10 + 122) * 2) / 3
     assert w["prep"][0] == pytest.approx({"f64": prep_flops})
     # k_face: 3 K P2 face-node pairs, 17 flux-precision values each
     assert w["face"][1] == 3 * K * P2 * 17 * 8
